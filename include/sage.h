@@ -1,0 +1,270 @@
+/*
+ * sage.h -- C-ABI of a B300-native runtime for many concurrent invocations of
+ * one GPU function that share one reference-counted device copy of the
+ * function's read-only data (SAGE, arXiv 2404.14691).
+ *
+ * Paper mapping
+ *   - Request / Data{key, Type ReadOnly|Writable, data_dptr} (Sec. 4.1, Sec. 5.2):
+ *     sage_fn_desc / sage_data_desc / sage_access.
+ *   - Unified memory daemon, one per GPU, that loads data proactively and hands
+ *     out device addresses (Sec. 3 overview, Sec. 4.1): sage_pool.
+ *   - Parallelised function setup: GPU data preparation runs beside the context /
+ *     module / workspace setup (Sec. 4.1, stages 3||4 and 5||6 of fig. workflow):
+ *     sage_prepare returns at once; staging runs on the pool's side stream and
+ *     host producer threads while the calling thread loads kernels and builds the
+ *     workspace.
+ *   - SageLoadToGPU returns the pointer before the data is ready; the kernel
+ *     executor checks readiness before launch (Sec. 4.2): sage_invoke makes the
+ *     launch stream wait on the data's ready event.
+ *   - Read-only memory sharing (Sec. 5.2): a second sage_prepare of the same key
+ *     takes a reference to the resident copy and loads nothing.
+ *   - Context memory sharing (Sec. 5.4): every invocation of a function runs in
+ *     one process / one CUDA context and reuses its kernels and workspace.
+ *
+ * The GPU function (the workload this runtime executes; the paper names no
+ * specific one) is a recommendation-style inference per sample b:
+ *     pooled[b, t*D:(t+1)*D] = sum over bag (t,b) of table_t rows
+ *     h = ReLU(... ReLU(x_b W0^T + b0) ...)              bottom MLP
+ *     c = [pooled[b, 0:T*D], h]                           concat
+ *     out[b] = sigmoid(top MLP(c)), ReLU after hidden top layers, last layer linear
+ *
+ * Conventions
+ *   - All functions return a sage_status; none throws or aborts.  On an error
+ *     sage_last_error() returns a thread-local message.
+ *   - "device" pointers are addresses in the pool's CUDA device; "host" pointers
+ *     are CPU addresses (pinned memory is faster but not required).
+ *   - Streams are cudaStream_t passed as void*; NULL means the legacy default stream.
+ *   - The library is thread-safe: a pool is protected by a mutex; invocations of
+ *     the same or different functions may be issued from any threads on any streams.
+ */
+#ifndef SAGE_H
+#define SAGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sage_pool_s* sage_pool;
+typedef struct sage_fn_s* sage_fn;
+
+typedef enum {
+    SAGE_OK = 0,
+    SAGE_PENDING = 1,          /* sage_fn_query: staging not finished yet (not an error) */
+    SAGE_ERR_INVALID = -1,     /* bad argument, or a key re-prepared with another shape */
+    SAGE_ERR_NOMEM = -2,       /* the pool's device-memory budget (or the device) is exhausted */
+    SAGE_ERR_CUDA = -3,        /* a CUDA call failed; see sage_last_error() */
+    SAGE_ERR_TIMEOUT = -4,     /* a bounded host wait ran out */
+    SAGE_ERR_BUSY = -5,        /* sage_pool_destroy with live references */
+    SAGE_ERR_STAGING = -6,     /* the producer of the read-only data failed; the handle is sticky-failed */
+    SAGE_ERR_BOUNDS = -7,      /* a kernel saw a bag row index outside its table (reported by sage_fn_check) */
+    SAGE_ERR_DEVICE = -8       /* a kernel's bounded wait ran out (reported by sage_fn_check) */
+} sage_status;
+
+/* Data.Type of the paper (Sec. 5.2): read-only data is shared between invocations. */
+typedef enum { SAGE_READONLY = 0, SAGE_WRITABLE = 1 } sage_access;
+
+/* Element type of the function's tables and weights.  SAGE_F32: fp32 tables,
+ * weights and activations.  SAGE_BF16: bf16 tables, weights and activations,
+ * fp32 accumulation on the tensor cores, fp32 biases, fp32 dense input. */
+typedef enum { SAGE_F32 = 0, SAGE_BF16 = 1 } sage_dtype;
+
+/* Device allocator hooks.  dev_alloc returns device memory of `bytes` usable on
+ * `stream` (a cudaStream_t) or NULL; dev_free returns it.  When both are NULL the
+ * pool uses cudaMallocAsync / cudaFreeAsync on its own side stream.  A Python
+ * caller may pass PyTorch's caching allocator here. */
+typedef void* (*sage_dev_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*sage_dev_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct {
+    int device;                    /* CUDA ordinal */
+    size_t budget_bytes;           /* device bytes the pool may hold for read-only data and
+                                      workspaces; 0 = free memory at creation minus 2 GiB */
+    size_t staging_chunk_bytes;    /* pinned staging chunk size; 0 = 64 MiB (rounded to 4 KiB) */
+    int staging_chunks;            /* pinned chunks in the ring; 0 = 4 */
+    int producer_threads;          /* host threads filling each chunk; 0 = min(16, cores) */
+    int serial_setup;              /* 1 = sage_prepare waits for staging before module /
+                                      workspace setup (the non-overlapped form, for comparison) */
+    sage_dev_alloc_fn dev_alloc;   /* optional */
+    sage_dev_free_fn dev_free;     /* optional; set both or neither */
+    void* alloc_ctx;
+} sage_pool_config;
+
+/* Producer of a data item: fill bytes [offset, offset+bytes) of the item into the
+ * host buffer dst.  offset and bytes are multiples of 256 except at the item's end.
+ * May be called concurrently from several host threads on disjoint ranges.
+ * Returns 0 on success, nonzero on failure (the item becomes sticky-failed). */
+typedef int (*sage_fill_fn)(void* dst, size_t offset, size_t bytes, void* ctx);
+
+/* One data item of a request (Data of Sec. 4.1 / 5.2).  Exactly one of host_src
+ * or fill must be set.  The caller keeps host_src (or fill_ctx) alive until
+ * sage_fn_wait returns SAGE_OK for a handle of this key (or the handle fails). */
+typedef struct {
+    const char* key;               /* unused for the two items of sage_fn_desc (the fn_key names both) */
+    sage_access access;            /* must be SAGE_READONLY for tables and weights */
+    size_t bytes;
+    const void* host_src;          /* host image of the item, or NULL */
+    sage_fill_fn fill;             /* producer, or NULL */
+    void* fill_ctx;
+} sage_data_desc;
+
+/* A GPU function: its shape and its read-only data.
+ *
+ * tables item: the T tables back to back, table t = rows[t] x dim elements of
+ *   `dtype`, row-major, no padding (bytes = sum(rows) * dim * elem).
+ * weights item: for each layer l in order (bottom layers, then top layers):
+ *   W_l [out_l x in_l] of `dtype`, row-major, then b_l [out_l] fp32; each of the
+ *   two arrays starts at a 256-byte aligned offset from the start of the item;
+ *   bytes = the end of the last bias rounded up to 256.
+ *   Bottom layer 0 has in = n_dense; top layer 0 has in = num_tables*dim +
+ *   bot_dims[n_bot-1]; the last top layer has out = 1.
+ * Limits: 1 <= num_tables <= 128; dim*elem a multiple of 16 bytes and <= 1024;
+ *   1 <= n_dense <= 64; n_bot, n_top in [1, 8]; for SAGE_BF16 every layer but
+ *   bottom 0 and the last top layer needs in and out multiples of 64 (tensor-core
+ *   tiles); rows[t] < 2^31. */
+typedef struct {
+    const char* fn_key;            /* identity of the read-only data (Data.key) */
+    sage_dtype dtype;
+    int num_tables;
+    const int64_t* rows;           /* [num_tables] */
+    int dim;
+    int n_dense;
+    int n_bot;
+    const int* bot_dims;           /* [n_bot] output sizes */
+    int n_top;
+    const int* top_dims;           /* [n_top] output sizes, last == 1 */
+    int max_batch;                 /* samples per workspace slot at prepare (grown on demand); 0 = 4096 */
+    int workspace_slots;           /* invocations in flight per function; 0 = 2 */
+    sage_data_desc tables;
+    sage_data_desc weights;
+} sage_fn_desc;
+
+/* One invocation (a request's writable data, all in device memory). */
+typedef struct {
+    int batch;                     /* B >= 0 samples */
+    const float* dense;            /* device [B, n_dense] fp32 row-major */
+    const int32_t* indices;        /* device: row indices of all bags */
+    const int64_t* offsets;        /* device [num_tables*B + 1], table-major CSR: bag (t,b) is
+                                      indices[offsets[t*B+b] .. offsets[t*B+b+1]) */
+    float* out;                    /* device [B]: sigmoid outputs */
+} sage_invocation;
+
+/* The same invocation with HOST buffers (Writable data loaded to the GPU and the
+ * result dumped back, SageLoadToGPU / SageDumpToDB of Sec. 4.2). */
+typedef struct {
+    int batch;
+    const float* dense;            /* host [B, n_dense] */
+    const int32_t* indices;        /* host [num_indices] */
+    const int64_t* offsets;        /* host [num_tables*B + 1], offsets[0] == 0 */
+    int64_t num_indices;           /* == offsets[num_tables*B] */
+    float* out;                    /* host [B] */
+} sage_host_invocation;
+
+typedef struct {
+    size_t budget_bytes;
+    size_t resident_bytes;         /* read-only data + workspaces currently held */
+    size_t readonly_bytes;         /* read-only data currently held */
+    int64_t functions;             /* resident function entries */
+    int64_t refs;                  /* live handles over all entries */
+    int64_t h2d_bytes;             /* read-only bytes staged host->device since creation */
+    int64_t prepares, hits, misses;
+    int64_t invocations;           /* invocations issued (a batch counts its members) */
+    int64_t launches;              /* kernels launched by the library */
+    double ctx_ms;                 /* context + pool creation time */
+    double last_stage_ms;          /* host time from prepare to the last chunk enqueued (last miss) */
+    double last_fill_ms;           /* producer time inside that staging */
+    double last_module_ms;         /* kernel loading + attribute setup of the last miss */
+    double last_workspace_ms;      /* workspace allocation + tensor-map setup of the last miss */
+    double last_prepare_ms;        /* wall time of the last sage_prepare call */
+} sage_pool_stats;
+
+/* Create a pool on config->device: makes the CUDA context current, creates the
+ * side (staging) stream, the pinned staging ring and the producer threads
+ * (the paper's "unified memory daemon", one per GPU).  config may be NULL. */
+sage_status sage_pool_create(const sage_pool_config* config, sage_pool* out);
+
+/* Prepare function desc->fn_key and return a new reference in *out.
+ * Resident key: takes a reference (no data loaded) -- read-only sharing, Sec. 5.2.
+ * New key: reserves budget (SAGE_ERR_NOMEM if over), allocates the device copy,
+ * queues the staging of tables and weights, then -- on the calling thread, while
+ * staging runs -- loads the kernels and allocates the workspace (Sec. 4.1).
+ * Returns without waiting for the data.  A resident key re-prepared with another
+ * dtype, shape or byte size returns SAGE_ERR_INVALID. */
+sage_status sage_prepare(sage_pool pool, const sage_fn_desc* desc, sage_fn* out);
+
+/* Non-blocking readiness query: SAGE_OK when the read-only data is on the device,
+ * SAGE_PENDING while staging, SAGE_ERR_STAGING after a producer failure. */
+sage_status sage_fn_query(sage_fn fn);
+
+/* Wait until the read-only data is on the device.  timeout_us < 0 waits forever.
+ * Returns SAGE_OK, SAGE_ERR_TIMEOUT or SAGE_ERR_STAGING. */
+sage_status sage_fn_wait(sage_fn fn, int64_t timeout_us);
+
+/* Run one invocation on `stream` (asynchronous).  The stream first waits, on the
+ * device, for the read-only data (the executor's readiness check, Sec. 4.2); the
+ * calling thread blocks only until the last staging copy has been queued.
+ * Returns SAGE_ERR_STAGING if the data failed to load. */
+sage_status sage_invoke(sage_fn fn, const sage_invocation* inv, void* stream);
+
+/* Run n invocations of the same function as ONE fused batch of sum(batch) samples
+ * on `stream`: one launch per layer / gather over all of them, outputs written to
+ * each invocation's own `out`.  Each result equals (bitwise) the result of
+ * invoking it alone. */
+sage_status sage_invoke_batch(sage_fn fn, const sage_invocation* invs, int n, void* stream);
+
+/* sage_invoke_batch with host buffers: copies each invocation's inputs to the
+ * device, runs the fused batch and copies the outputs back, all on `stream`;
+ * returns after the outputs are in host memory. */
+sage_status sage_invoke_batch_host(sage_fn fn, const sage_host_invocation* invs, int n, void* stream);
+
+/* Read and clear the function's device error word after synchronising it:
+ * SAGE_OK, SAGE_ERR_BOUNDS (a bag row index was outside its table; the row was
+ * skipped) or SAGE_ERR_DEVICE (a kernel's bounded wait ran out). */
+sage_status sage_fn_check(sage_fn fn);
+
+/* Drop a reference.  When the last reference of a key is dropped, the pool waits
+ * for the key's in-flight work, frees its device copy and workspace and returns
+ * the budget (the paper's release after the last invocation, Sec. 5.3). */
+sage_status sage_release(sage_fn fn);
+
+/* Destroy an empty pool; SAGE_ERR_BUSY while any reference is live. */
+sage_status sage_pool_destroy(sage_pool pool);
+
+sage_status sage_pool_stats_get(sage_pool pool, sage_pool_stats* out);
+
+/* Thread-local message of the last error returned on this thread ("" if none). */
+const char* sage_last_error(void);
+
+/* Number of kernels the library has launched in this process (all pools). */
+int64_t sage_kernel_launches(void);
+
+/* ---- building blocks (the kernels of sage_invoke, callable one by one) ----
+ * Used by the parity tests and the kernel benchmarks.  All pointers are device
+ * pointers; all calls are asynchronous on `stream`; err_word (device int, may be
+ * NULL) receives bit 1 on an out-of-range row and bit 2 on a timed-out wait. */
+
+/* Embedding-bag sum (the gather of the function):
+ *   out[b*ldo + t*dim + d] = sum_{i in [offsets[t*B+b], offsets[t*B+b+1])} table_t[indices[i]*dim + d]
+ * tables: the tables item (back to back, `dtype`); table_rows [T] on the host;
+ * out: fp32 for SAGE_F32, bf16 (round to nearest even) for SAGE_BF16, row stride
+ * ldo elements.  Sums run in fp32 in a fixed order (independent of B).
+ * uniform-length bags, index layout and ranges as in sage_invocation. */
+sage_status sage_embedding_bag_sum(sage_dtype dtype, const void* tables, const int64_t* table_rows,
+                                   int num_tables, int dim, int batch, const int32_t* indices,
+                                   const int64_t* offsets, void* out, int ldo, int* err_word,
+                                   void* stream);
+
+/* Linear layer y = act(x W^T + bias) for M rows: x [M, K] (row stride ldx),
+ * W [N, K] row-major, bias [N] fp32, y [M, N] (row stride ldy); act 0 = none,
+ * 1 = ReLU.  SAGE_F32: fp32 in/out, fp32 FMA in a fixed K order.  SAGE_BF16:
+ * bf16 in/out, tcgen05 tensor cores with fp32 accumulation in tensor memory;
+ * needs K and N multiples of 64 and 16-byte aligned rows. */
+sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,
+                        const float* bias, int act, void* y, int ldy, int* err_word, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SAGE_H */

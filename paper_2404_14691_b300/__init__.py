@@ -1,0 +1,155 @@
+"""B300-native runtime for many concurrent invocations of one GPU function that
+share one reference-counted device copy of its read-only data (SAGE,
+arXiv 2404.14691), with hand-written sm_103a kernels for the function itself
+(an embedding-bag gather-sum and bottom/top MLPs).
+
+This package is a thin ctypes binding over libsage.so (include/sage.h): it
+marshals arguments and holds Python-side references; every step of the hot
+path runs in the library's CUDA kernels.  PyTorch is used only for device
+memory (optional allocator hooks) and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+from ._native import (DEV_ALLOC_FN, DEV_FREE_FN, SAGE_BF16, SAGE_F32, SAGE_OK, SAGE_PENDING, SAGE_READONLY,
+                      STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, PoolConfig, PoolStats, SageError,
+                      check, lib)
+
+__all__ = ["Pool", "Function", "SageError", "SAGE_F32", "SAGE_BF16", "embedding_bag_sum", "linear",
+           "kernel_launches", "torch_allocator_hooks"]
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libsage.so in this process."""
+    return int(lib().sage_kernel_launches())
+
+
+def torch_allocator_hooks(device: int = 0):
+    """(alloc, free) C callbacks routing the pool's device memory through PyTorch's
+    caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream or 0)
+        except Exception:  # out of memory -> NULL, reported as SAGE_ERR_NOMEM
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return DEV_ALLOC_FN(_alloc), DEV_FREE_FN(_free)
+
+
+class Function:
+    """A reference to a prepared function (sage_fn)."""
+
+    def __init__(self, pool: "Pool", handle: int, keep):
+        self.pool = pool
+        self.handle = ctypes.c_void_p(handle)
+        self._keep = keep
+
+    def query(self) -> int:
+        return check(lib().sage_fn_query(self.handle), "sage_fn_query")
+
+    def wait(self, timeout_us: int = -1) -> None:
+        check(lib().sage_fn_wait(self.handle, int(timeout_us)), "sage_fn_wait")
+
+    def invoke(self, batch: int, dense: int, indices: int, offsets: int, out: int, stream=None) -> None:
+        inv = Invocation(int(batch), dense, indices, offsets, out)
+        check(lib().sage_invoke(self.handle, ctypes.byref(inv), _stream_handle(stream)), "sage_invoke")
+
+    def invoke_batch(self, invs: Sequence[tuple], stream=None) -> None:
+        """invs: (batch, dense_ptr, indices_ptr, offsets_ptr, out_ptr) per invocation (device pointers)."""
+        arr = (Invocation * len(invs))(*[Invocation(int(b), d, i, o, u) for (b, d, i, o, u) in invs])
+        check(lib().sage_invoke_batch(self.handle, arr, len(invs), _stream_handle(stream)), "sage_invoke_batch")
+
+    def invoke_batch_host(self, invs: Sequence[tuple], stream=None) -> None:
+        """invs: (batch, dense_ptr, indices_ptr, offsets_ptr, num_indices, out_ptr) per invocation (host pointers)."""
+        arr = (HostInvocation * len(invs))(*[HostInvocation(int(b), d, i, o, int(n), u)
+                                             for (b, d, i, o, n, u) in invs])
+        check(lib().sage_invoke_batch_host(self.handle, arr, len(invs), _stream_handle(stream)),
+              "sage_invoke_batch_host")
+
+    def check_errors(self) -> None:
+        """Raise SageError if a kernel saw an out-of-range row or a timed-out wait."""
+        check(lib().sage_fn_check(self.handle), "sage_fn_check")
+
+    def release(self) -> None:
+        if self.handle is not None:
+            check(lib().sage_release(self.handle), "sage_release")
+            self.handle = None
+            self._keep = None
+
+
+class Pool:
+    """A per-GPU pool of read-only function data (sage_pool)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, staging_chunk_bytes: int = 0,
+                 staging_chunks: int = 0, producer_threads: int = 0, serial_setup: bool = False,
+                 torch_allocator: bool = False):
+        self._hooks = torch_allocator_hooks(device) if torch_allocator else None
+        cfg = PoolConfig(device, budget_bytes, staging_chunk_bytes, staging_chunks, producer_threads,
+                         1 if serial_setup else 0,
+                         ctypes.cast(self._hooks[0], ctypes.c_void_p) if self._hooks else None,
+                         ctypes.cast(self._hooks[1], ctypes.c_void_p) if self._hooks else None, None)
+        h = ctypes.c_void_p()
+        check(lib().sage_pool_create(ctypes.byref(cfg), ctypes.byref(h)), "sage_pool_create")
+        self.handle = h
+
+    def prepare(self, key: str, dtype: int, rows: Sequence[int], dim: int, n_dense: int,
+                bot_dims: Sequence[int], top_dims: Sequence[int], tables_bytes: int, weights_bytes: int,
+                tables_src: Optional[int] = None, tables_fill: Optional[int] = None, tables_ctx=None,
+                weights_src: Optional[int] = None, max_batch: int = 0, workspace_slots: int = 0,
+                keep=None) -> Function:
+        """Prepare a function.  tables_src / weights_src: host addresses of the data
+        items; or tables_fill: address of a C producer (sage_fill_fn) with tables_ctx."""
+        T = len(rows)
+        rows_a = (ctypes.c_int64 * T)(*rows)
+        bot_a = (ctypes.c_int * len(bot_dims))(*bot_dims)
+        top_a = (ctypes.c_int * len(top_dims))(*top_dims)
+        kb = key.encode()
+        ctx_ptr = ctypes.cast(ctypes.byref(tables_ctx), ctypes.c_void_p) if tables_ctx is not None else None
+        tdesc = DataDesc(kb, SAGE_READONLY, tables_bytes, tables_src, tables_fill, ctx_ptr)
+        wdesc = DataDesc(kb, SAGE_READONLY, weights_bytes, weights_src, None, None)
+        d = FnDesc(kb, dtype, T, rows_a, dim, n_dense, len(bot_dims), bot_a, len(top_dims), top_a,
+                   max_batch, workspace_slots, tdesc, wdesc)
+        h = ctypes.c_void_p()
+        check(lib().sage_prepare(self.handle, ctypes.byref(d), ctypes.byref(h)), "sage_prepare")
+        return Function(self, h.value, (rows_a, bot_a, top_a, kb, tables_ctx, keep))
+
+    def stats(self) -> dict:
+        s = PoolStats()
+        check(lib().sage_pool_stats_get(self.handle, ctypes.byref(s)), "sage_pool_stats_get")
+        return {name: getattr(s, name) for name, _ in PoolStats._fields_}
+
+    def destroy(self) -> None:
+        if self.handle is not None:
+            check(lib().sage_pool_destroy(self.handle), "sage_pool_destroy")
+            self.handle = None
+
+
+def embedding_bag_sum(dtype: int, tables: int, table_rows: Sequence[int], dim: int, batch: int, indices: int,
+                      offsets: int, out: int, ldo: int, err_word: Optional[int] = None, stream=None) -> None:
+    """sage_embedding_bag_sum on device pointers."""
+    T = len(table_rows)
+    rows_a = (ctypes.c_int64 * T)(*table_rows)
+    check(lib().sage_embedding_bag_sum(dtype, tables, rows_a, T, dim, batch, indices, offsets, out, ldo, err_word,
+                                       _stream_handle(stream)), "sage_embedding_bag_sum")
+
+
+def linear(dtype: int, M: int, N: int, K: int, x: int, ldx: int, W: int, bias: int, relu: bool, y: int, ldy: int,
+           err_word: Optional[int] = None, stream=None) -> None:
+    """sage_linear on device pointers."""
+    check(lib().sage_linear(dtype, M, N, K, x, ldx, W, bias, 1 if relu else 0, y, ldy, err_word,
+                            _stream_handle(stream)), "sage_linear")

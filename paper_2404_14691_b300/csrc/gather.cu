@@ -1,0 +1,184 @@
+// Embedding-bag gather-sum over a fused batch of invocations (HBM-bound).
+//
+// Each warp owns one bag at a time (grid-stride over the T*M bags of the batch,
+// table-major so that neighbouring warps read the same table).  A row of the
+// table is LPR lanes x 16 bytes; a warp therefore reads RPW = 32/LPR rows per
+// load instruction and keeps U such instructions in flight.  Row indices are
+// fetched 32 at a time with one coalesced load and broadcast with shuffles.
+// Sub-group s of the warp sums the bag positions p with p % RPW == s in position
+// order; the RPW partial sums are then combined by a fixed xor tree.  The order
+// of every sum therefore depends only on the bag itself, never on the batch it
+// runs in, which makes fused and isolated invocations bitwise identical.
+#include "kernels.h"
+
+namespace sage {
+namespace {
+
+template <int N>
+struct Acc {
+  float v[N];
+};
+
+__device__ __forceinline__ uint4 ldg_nc_v4(const uint4* p) { return __ldg(p); }
+
+template <bool BF16, int LPR, int VPL, int U>
+__global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a,
+                                                     const __grid_constant__ InvTable tab) {
+  constexpr int RPW = 32 / LPR;
+  constexpr int EPV = BF16 ? 8 : 4;  // elements per 16-byte vector
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / LPR;
+  const int col = lane % LPR;
+  const int64_t G = static_cast<int64_t>(a.T) * tab.M;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  const size_t row_bytes = static_cast<size_t>(a.dim) * (BF16 ? 2 : 4);
+
+  for (int64_t g = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; g < G; g += nwarps) {
+    const int t = static_cast<int>(g / tab.M);
+    const int r = static_cast<int>(g - static_cast<int64_t>(t) * tab.M);
+    const int i = tab.n == 1 ? 0 : find_inv(tab, r);
+    const InvDesc& d = tab.d[i];
+    const int64_t bag = static_cast<int64_t>(t) * d.batch + (r - d.row_base);
+    const int64_t beg = d.offsets[bag];
+    const int64_t end = d.offsets[bag + 1];
+    const char* base = a.tables + a.table_off[t];
+    const unsigned rows = static_cast<unsigned>(a.table_rows[t]);
+
+    float acc[VPL][EPV];
+#pragma unroll
+    for (int w = 0; w < VPL; ++w)
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
+
+    for (int64_t j0 = beg; j0 < end; j0 += 32) {
+      const int cnt = static_cast<int>(min(static_cast<int64_t>(32), end - j0));
+      const int my = lane < cnt ? __ldg(d.indices + j0 + lane) : 0;
+      for (int q = 0; q < cnt; q += RPW * U) {
+        uint4 v[U][VPL];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int p = q + u * RPW + sub;
+          const int row = __shfl_sync(0xffffffffu, my, p & 31);
+          ok[u] = p < cnt;
+          if (ok[u] && static_cast<unsigned>(row) >= rows) {
+            ok[u] = false;
+            if (a.err) atomicOr(a.err, kErrBounds);
+          }
+          const uint4* src = reinterpret_cast<const uint4*>(base + static_cast<size_t>(ok[u] ? row : 0) * row_bytes) + col;
+#pragma unroll
+          for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w * LPR) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!ok[u]) continue;
+#pragma unroll
+          for (int w = 0; w < VPL; ++w) {
+            if (BF16) {
+              const uint32_t wd[4] = {v[u][w].x, v[u][w].y, v[u][w].z, v[u][w].w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 f = unpack_bf16x2(wd[e]);
+                acc[w][2 * e] += f.x;
+                acc[w][2 * e + 1] += f.y;
+              }
+            } else {
+              acc[w][0] += __uint_as_float(v[u][w].x);
+              acc[w][1] += __uint_as_float(v[u][w].y);
+              acc[w][2] += __uint_as_float(v[u][w].z);
+              acc[w][3] += __uint_as_float(v[u][w].w);
+            }
+          }
+        }
+      }
+    }
+    // combine the RPW sub-group partial sums (fixed tree; a+b == b+a exactly)
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+      for (int w = 0; w < VPL; ++w)
+#pragma unroll
+        for (int e = 0; e < EPV; ++e) acc[w][e] += __shfl_xor_sync(0xffffffffu, acc[w][e], o);
+
+    if (sub == 0) {
+      char* orow = static_cast<char*>(a.out) +
+                   (static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim) * (BF16 ? 2 : 4);
+#pragma unroll
+      for (int w = 0; w < VPL; ++w) {
+        uint4 o;
+        if (BF16) {
+          o.x = pack_bf16x2(acc[w][0], acc[w][1]);
+          o.y = pack_bf16x2(acc[w][2], acc[w][3]);
+          o.z = pack_bf16x2(acc[w][4], acc[w][5]);
+          o.w = pack_bf16x2(acc[w][6], acc[w][7]);
+        } else {
+          o = make_uint4(__float_as_uint(acc[w][0]), __float_as_uint(acc[w][1]), __float_as_uint(acc[w][2]),
+                         __float_as_uint(acc[w][3]));
+        }
+        reinterpret_cast<uint4*>(orow)[col + w * LPR] = o;
+      }
+    }
+  }
+}
+
+template <bool BF16, int LPR, int VPL, int U>
+cudaError_t launch_one(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
+  static int blocks_per_sm = -1, sms = 0;
+  if (blocks_per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_kernel<BF16, LPR, VPL, U>, 256, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int64_t bags = static_cast<int64_t>(a.T) * tab.M;
+  if (bags == 0) return cudaSuccess;
+  int64_t need = (bags + 7) / 8;
+  int64_t grid = static_cast<int64_t>(sms) * blocks_per_sm;
+  if (need < grid) grid = need;
+  gather_kernel<BF16, LPR, VPL, U><<<static_cast<unsigned>(grid), 256, 0, s>>>(a, tab);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <bool BF16>
+cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
+  const int rb = a.dim * (BF16 ? 2 : 4);
+  switch (rb) {
+    case 16: return launch_one<BF16, 1, 1, 1>(a, tab, s);
+    case 32: return launch_one<BF16, 2, 1, 1>(a, tab, s);
+    case 64: return launch_one<BF16, 4, 1, 2>(a, tab, s);
+    case 128: return launch_one<BF16, 8, 1, 4>(a, tab, s);
+    case 256: return launch_one<BF16, 16, 1, 8>(a, tab, s);
+    case 512: return launch_one<BF16, 32, 1, 8>(a, tab, s);
+    case 1024: return launch_one<BF16, 32, 2, 4>(a, tab, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+void preload_gather_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 1, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 2, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 4, 1, 2>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 1, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 16, 1, 8>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 1, 8>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 2, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 1, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 2, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 4, 1, 2>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 8, 1, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 16, 1, 8>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 1, 8>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 2, 4>);
+}
+
+cudaError_t launch_gather(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
+  if (a.T < 1 || a.T > kMaxTables || tab.n < 1 || tab.n > kMaxInv) return cudaErrorInvalidValue;
+  return a.dtype == 1 ? dispatch<true>(a, tab, s) : dispatch<false>(a, tab, s);
+}
+
+}  // namespace sage

@@ -1,0 +1,214 @@
+// BF16 GEMM on the 5th-generation tensor cores (tcgen05) with TMA operand loads:
+//     Y[M, N] = act(X[M, K] W[N, K]^T + b),  fp32 accumulation in tensor memory.
+//
+// One CTA computes a 128 x BN tile with 4 warps:
+//   warp 0, one lane : TMA producer -- streams 128x64 tiles of X and BNx64 tiles of
+//                      W (128-byte swizzle) into a STAGES-deep shared-memory ring;
+//   warp 1, one lane : MMA issuer -- 4 tcgen05.mma (K = 16 each) per stage into a
+//                      128 x BN fp32 accumulator in tensor memory; tcgen05.commit
+//                      frees each stage and finally signals the epilogue;
+//   all 4 warps      : epilogue -- tcgen05.ld of the warp's 32 TMEM lanes (= rows),
+//                      bias, ReLU, round to bf16, 16-byte stores (possibly into a
+//                      column slice of a wider buffer, e.g. the concat buffer).
+// Every wait is bounded (see mbar_wait); a timed-out wait sets kErrTimeout in
+// the caller's error word and the CTA finishes without hanging.  The K
+// accumulation order of an output element is fixed (k-steps of 16 in order),
+// so a row's result does not depend on M or on the other rows of the batch.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "kernels.h"
+
+namespace sage {
+namespace {
+
+constexpr int kBM = 128, kBK = 64;
+constexpr int kPipeBytes = 192 * 1024;
+
+template <int BN>
+struct TcCfg {
+  static constexpr int A_BYTES = kBM * kBK * 2;
+  static constexpr int B_BYTES = BN * kBK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = kPipeBytes / STAGE;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                   int K, const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ Y, int ldy,
+                   int* err) {
+  using C = TcCfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + C::STAGES * C::A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + C::STAGES * C::B_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accum = empty + C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
+  const int KB = (K + kBK - 1) / kBK;
+
+  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  if (warp == 1 && lane == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 2 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (kb / C::STAGES) & 1;
+      if (!mbar_wait(&empty[s], ph ^ 1, err)) break;
+      mbar_arrive_expect_tx(&full[s], C::STAGE);
+      tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * kBK, m0, &full[s]);
+      tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * kBK, n0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (kb / C::STAGES) & 1;
+      if (!mbar_wait(&full[s], ph, err)) break;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * C::A_BYTES);
+      const uint32_t b0 = smem_u32(sB + s * C::B_BYTES);
+#pragma unroll
+      for (int k = 0; k < kBK / 16; ++k) {
+        tc_mma_bf16(tmem, sw128_kmajor_desc(a0 + k * 32), sw128_kmajor_desc(b0 + k * 32), idesc,
+                    (kb | k) != 0 ? 1u : 0u);
+      }
+      tc_commit(&empty[s]);
+    }
+    tc_commit(accum);
+  }
+  __syncwarp();
+
+  // ---- epilogue: TMEM -> registers -> bias/ReLU -> bf16 -> global
+  mbar_wait(accum, 0, err);
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  __nv_bfloat16* yrow = Y + static_cast<size_t>(row < M ? row : 0) * ldy + n0;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld_32cols(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+    tmem_ld_wait();
+    if (row < M) {
+      uint32_t pk[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float f0 = __uint_as_float(v[2 * j]) + __ldg(bias + n0 + c0 + 2 * j);
+        float f1 = __uint_as_float(v[2 * j + 1]) + __ldg(bias + n0 + c0 + 2 * j + 1);
+        if (relu) {
+          f0 = fmaxf(f0, 0.f);
+          f1 = fmaxf(f1, 0.f);
+        }
+        pk[j] = pack_bf16x2(f0, f1);
+      }
+      uint4* dst = reinterpret_cast<uint4*>(yrow + c0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Row-major bf16 matrix [rows, cols] with row stride ld elements, tiles of
+// box_rows x 64 columns, 128-byte swizzle, zero fill outside the matrix.
+bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
+  auto enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * 2};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias, int relu,
+                      void* y, int ldy, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<BN>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
+  dim3 grid(N / BN, (M + kBM - 1) / kBM);
+  gemm_tc_kernel<BN><<<grid, 128, TcCfg<BN>::SMEM, s>>>(ta, tb, M, N, K, bias, relu,
+                                                       static_cast<__nv_bfloat16*>(y), ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+void preload_tc_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<64>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<128>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<256>);
+  encode_fn();
+}
+
+cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, const void* W,
+                                  const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  if (K <= 0 || (K % kBK) || (N % 64) || (ldx % 8) || (ldy % 8) ||
+      (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(W) & 15) ||
+      (reinterpret_cast<uintptr_t>(y) & 15))
+    return cudaErrorInvalidValue;
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int mt = (M + kBM - 1) / kBM;
+  if (N % 256 == 0 && mt * (N / 256) >= g_sms) return launch_bn<256>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  return launch_bn<64>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+}
+
+}  // namespace sage

@@ -1,0 +1,50 @@
+// Host-side launch interface of the sm_103a kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sage {
+
+// Kernels launched by this library so far (all pools, all threads).
+void count_launch(int n = 1);
+int64_t launches();
+
+// Embedding-bag sum over a fused batch (the gather of the function).
+struct GatherArgs {
+  int dtype;                         // 0 fp32 tables/out, 1 bf16 tables/out
+  const char* tables;                // tables item
+  int64_t table_off[kMaxTables];     // byte offset of table t in the item
+  int32_t table_rows[kMaxTables];
+  int T;
+  int dim;
+  void* out;                         // [M, ldo] elements of the table dtype
+  int ldo;
+  int* err;
+};
+cudaError_t launch_gather(const GatherArgs& a, const InvTable& tab, cudaStream_t s);
+
+// Bottom layer 0: y = ReLU(dense W0^T + b0) with the dense rows read from each
+// invocation of the batch.  W0 [N, K] in the dtype, y [M, ldy] in the dtype.
+cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const void* W, const float* bias,
+                           void* y, int ldy, cudaStream_t s);
+
+// Head: out_i[b] = sigmoid(h[r, :] . w + c) for every row r of the batch, written
+// to its invocation's out.  h [M, ldh] in the dtype, w [K] in the dtype, c fp32.
+cudaError_t launch_head(int dtype, const InvTable& tab, int K, const void* h, int ldh, const void* w,
+                        const float* c, cudaStream_t s);
+
+// Dense layers y = act(x W^T + b).
+cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
+                              int relu, float* y, int ldy, cudaStream_t s);
+cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, const void* W,
+                                  const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s);
+
+// Kernel loading: query every kernel of a translation unit once, which makes the
+// CUDA runtime load its module (lazy loading defers this to first use).
+void preload_gather_kernels();
+void preload_simt_kernels();
+void preload_tc_kernels();
+
+}  // namespace sage

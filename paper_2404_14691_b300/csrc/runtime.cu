@@ -1,0 +1,1157 @@
+// Runtime behind the C-ABI of include/sage.h: the per-GPU pool (the paper's
+// unified memory daemon, Sec. 3/4.1), read-only sharing by key with reference
+// counts (Sec. 5.2), staging of read-only data through a pinned ring on a side
+// stream while the calling thread loads kernels and builds workspaces
+// (parallelised setup, Sec. 4.1), the readiness gate before launch (Sec. 4.2),
+// and the invocation chain of the recommendation-style function.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <functional>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "../../include/sage.h"
+#include "kernels.h"
+
+namespace sage {
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace sage
+
+using namespace sage;
+
+namespace {
+
+thread_local std::string t_err;
+
+sage_status fail(sage_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return st;
+}
+
+#define SAGE_CK(call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess)                                                                             \
+      return fail(SAGE_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+using Clock = std::chrono::steady_clock;
+double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------- host workers
+// A fixed set of threads that run fn(i) for i in [0, n) together with the caller.
+class Workers {
+ public:
+  explicit Workers(int n) {
+    for (int i = 0; i < n; ++i) th_.emplace_back([this] { loop(); });
+  }
+  ~Workers() {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto& t : th_) t.join();
+  }
+  void parallel_for(int n, const std::function<void(int)>& fn) {
+    std::unique_lock<std::mutex> g(job_mu_);  // one job at a time
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      fn_ = &fn;
+      n_ = n;
+      next_ = 0;
+      done_ = 0;
+      ++gen_;
+    }
+    cv_.notify_all();
+    run_items();
+    std::unique_lock<std::mutex> l(mu_);
+    done_cv_.wait(l, [&] { return done_ == n_; });
+    fn_ = nullptr;
+  }
+  int size() const { return static_cast<int>(th_.size()) + 1; }
+
+ private:
+  void run_items() {
+    for (;;) {
+      int i;
+      const std::function<void(int)>* f;
+      {
+        std::lock_guard<std::mutex> l(mu_);
+        if (!fn_ || next_ >= n_) return;
+        i = next_++;
+        f = fn_;
+      }
+      (*f)(i);
+      {
+        std::lock_guard<std::mutex> l(mu_);
+        if (++done_ == n_) done_cv_.notify_all();
+      }
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> l(mu_);
+        cv_.wait(l, [&] { return stop_ || (gen_ != seen && fn_ && next_ < n_); });
+        if (stop_) return;
+        seen = gen_;
+      }
+      run_items();
+    }
+  }
+  std::vector<std::thread> th_;
+  std::mutex mu_, job_mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int n_ = 0, next_ = 0, done_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
+
+struct Layer {
+  int in, out;
+  const void* W;
+  const float* b;
+};
+
+// One invocation slot: activations for `cap` rows and an I/O arena for host
+// invocations; `done` orders the slot's reuse across streams.
+struct Slot {
+  int cap = 0;
+  char* buf = nullptr;
+  size_t bytes = 0;
+  std::vector<char*> bot;  // bottom hidden outputs except the last layer's
+  char* concat = nullptr;
+  std::vector<char*> top;  // top hidden outputs except the head's
+  char* io = nullptr;
+  size_t io_bytes = 0;
+  cudaEvent_t done = nullptr;
+  bool used = false;
+};
+
+}  // namespace
+
+struct sage_pool_s;
+
+struct Entry {
+  sage_pool_s* pool = nullptr;
+  std::string key;
+  int dtype = 0, T = 0, dim = 0, n_dense = 0;
+  std::vector<int64_t> rows;
+  std::vector<int> bot, top;
+  size_t tables_bytes = 0, weights_bytes = 0, reserved = 0, ws_bytes = 0;
+  char* d_tables = nullptr;
+  char* d_weights = nullptr;
+  int* d_err = nullptr;
+  std::vector<Layer> layers;
+  int64_t table_off[kMaxTables] = {};
+  int refs = 0;
+
+  // staging (the read-only data's journey host -> device)
+  sage_data_desc tdesc{}, wdesc{};
+  std::mutex smu;
+  std::condition_variable scv;
+  int sstate = 0;      // 0 queued/copying, 1 all copies queued (ready event recorded), 2 failed
+  int setup = 0;       // 0 building, 1 ready, 2 failed
+  bool cancel = false;
+  bool queued = false;
+  cudaEvent_t ready = nullptr;
+  Clock::time_point t_prepare;
+  double stage_ms = 0, fill_ms = 0;
+  int64_t staged_bytes = 0;
+
+  // invocations
+  std::mutex imu;
+  std::vector<Slot> slots;
+  int next_slot = 0;
+  int max_batch = 4096;
+
+  int concat_dim() const { return T * dim + bot.back(); }
+  size_t elem() const { return dtype == SAGE_BF16 ? 2 : 4; }
+};
+
+struct sage_fn_s {
+  sage_pool_s* pool;
+  Entry* e;
+  uint64_t magic;
+};
+static constexpr uint64_t kFnMagic = 0x5A6E5F66756E6331ull;
+
+struct sage_pool_s {
+  int device = 0;
+  size_t budget = 0, used = 0;
+  sage_dev_alloc_fn dalloc = nullptr;
+  sage_dev_free_fn dfree = nullptr;
+  void* actx = nullptr;
+  bool serial_setup = false;
+  cudaStream_t side = nullptr;
+  size_t chunk_bytes = 0;
+  std::vector<char*> ring;
+  std::vector<cudaEvent_t> ring_ev;
+  size_t ring_next = 0;
+  std::unique_ptr<Workers> workers;
+  std::thread stager;
+  std::mutex qmu;
+  std::condition_variable qcv;
+  std::deque<Entry*> queue;
+  bool stop = false;
+  std::mutex mu;
+  std::unordered_map<std::string, Entry*> entries;
+  std::unordered_set<sage_fn_s*> handles;
+  sage_pool_stats st{};
+  std::atomic<int64_t> h2d{0}, invocations{0};
+
+  void* dev_alloc(size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 256;
+    if (dalloc) return dalloc(bytes, s, actx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void dev_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (dfree) dfree(p, bytes, s, actx);
+    else cudaFreeAsync(p, s);
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------- staging daemon
+
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+// Stage one data item into dst: fill pinned ring chunks on the host workers and
+// copy each on the side stream; a chunk is refilled only after its previous
+// copy finished.  Returns false if the producer failed or staging was cancelled.
+bool stage_item(sage_pool_s* P, Entry* e, const sage_data_desc& d, char* dst, double* fill_ms) {
+  if (d.bytes == 0) return true;
+  if (d.host_src && is_pinned(d.host_src)) {
+    if (cudaMemcpyAsync(dst, d.host_src, d.bytes, cudaMemcpyHostToDevice, P->side) != cudaSuccess) return false;
+    P->h2d += static_cast<int64_t>(d.bytes);
+    e->staged_bytes += static_cast<int64_t>(d.bytes);
+    return true;
+  }
+  const int parts_per_chunk = P->workers->size();
+  for (size_t off = 0; off < d.bytes; off += P->chunk_bytes) {
+    {
+      std::lock_guard<std::mutex> g(e->smu);
+      if (e->cancel) return false;
+    }
+    const size_t n = std::min(P->chunk_bytes, d.bytes - off);
+    const size_t k = P->ring_next++ % P->ring.size();
+    if (cudaEventSynchronize(P->ring_ev[k]) != cudaSuccess) return false;
+    char* buf = P->ring[k];
+    std::atomic<int> bad{0};
+    const size_t part = align256((n + parts_per_chunk - 1) / parts_per_chunk);
+    const int nparts = static_cast<int>((n + part - 1) / part);
+    auto t0 = Clock::now();
+    P->workers->parallel_for(nparts, [&](int i) {
+      const size_t p0 = static_cast<size_t>(i) * part;
+      const size_t pn = std::min(part, n - p0);
+      if (d.host_src) {
+        memcpy(buf + p0, static_cast<const char*>(d.host_src) + off + p0, pn);
+      } else if (d.fill(buf + p0, off + p0, pn, d.fill_ctx) != 0) {
+        bad.store(1);
+      }
+    });
+    *fill_ms += ms_since(t0);
+    if (bad.load()) return false;
+    if (cudaMemcpyAsync(dst + off, buf, n, cudaMemcpyHostToDevice, P->side) != cudaSuccess) return false;
+    if (cudaEventRecord(P->ring_ev[k], P->side) != cudaSuccess) return false;
+    P->h2d += static_cast<int64_t>(n);
+    e->staged_bytes += static_cast<int64_t>(n);
+  }
+  return true;
+}
+
+void stage_entry(sage_pool_s* P, Entry* e) {
+  double fill_ms = 0;
+  bool ok = stage_item(P, e, e->wdesc, e->d_weights, &fill_ms) &&
+            stage_item(P, e, e->tdesc, e->d_tables, &fill_ms);
+  // the ready event covers every copy queued for this entry, also on failure
+  if (cudaEventRecord(e->ready, P->side) != cudaSuccess) ok = false;
+  const double stage_ms = ms_since(e->t_prepare);
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    P->st.last_stage_ms = stage_ms;
+    P->st.last_fill_ms = fill_ms;
+  }
+  std::lock_guard<std::mutex> g(e->smu);
+  e->stage_ms = stage_ms;
+  e->fill_ms = fill_ms;
+  e->sstate = ok ? 1 : 2;
+  e->scv.notify_all();
+}
+
+void stager_loop(sage_pool_s* P) {
+  cudaSetDevice(P->device);
+  for (;;) {
+    Entry* e;
+    {
+      std::unique_lock<std::mutex> l(P->qmu);
+      P->qcv.wait(l, [&] { return P->stop || !P->queue.empty(); });
+      if (P->queue.empty()) return;
+      e = P->queue.front();
+      P->queue.pop_front();
+    }
+    stage_entry(P, e);
+  }
+}
+
+// ---------------------------------------------------------------- kernels / workspace
+
+std::once_flag g_load_once;
+double g_load_ms = 0;
+
+double load_kernels_once() {
+  double spent = 0;
+  std::call_once(g_load_once, [&] {
+    auto t0 = Clock::now();
+    preload_gather_kernels();
+    preload_simt_kernels();
+    preload_tc_kernels();
+    g_load_ms = ms_since(t0);
+    spent = g_load_ms;
+  });
+  return spent;
+}
+
+size_t slot_bytes(const Entry* e, int cap) {
+  size_t b = 0;
+  for (size_t l = 0; l + 1 < e->bot.size(); ++l) b += align256(static_cast<size_t>(cap) * e->bot[l] * e->elem());
+  b += align256(static_cast<size_t>(cap) * e->concat_dim() * e->elem());
+  for (size_t l = 0; l + 1 < e->top.size(); ++l) b += align256(static_cast<size_t>(cap) * e->top[l] * e->elem());
+  return b;
+}
+
+sage_status build_slot(Entry* e, Slot& s, int cap, cudaStream_t stream) {
+  sage_pool_s* P = e->pool;
+  const size_t bytes = slot_bytes(e, cap);
+  char* buf = static_cast<char*>(P->dev_alloc(bytes, stream));
+  if (!buf) return fail(SAGE_ERR_NOMEM, "workspace allocation of %zu bytes failed", bytes);
+  if (s.buf) P->dev_free(s.buf, s.bytes, stream);
+  s.buf = buf;
+  s.bytes = bytes;
+  s.cap = cap;
+  s.bot.clear();
+  s.top.clear();
+  size_t o = 0;
+  for (size_t l = 0; l + 1 < e->bot.size(); ++l) {
+    s.bot.push_back(buf + o);
+    o += align256(static_cast<size_t>(cap) * e->bot[l] * e->elem());
+  }
+  s.concat = buf + o;
+  o += align256(static_cast<size_t>(cap) * e->concat_dim() * e->elem());
+  for (size_t l = 0; l + 1 < e->top.size(); ++l) {
+    s.top.push_back(buf + o);
+    o += align256(static_cast<size_t>(cap) * e->top[l] * e->elem());
+  }
+  return SAGE_OK;
+}
+
+sage_status check_desc(const sage_fn_desc* d) {
+  if (!d || !d->fn_key) return fail(SAGE_ERR_INVALID, "null descriptor or key");
+  if (d->dtype != SAGE_F32 && d->dtype != SAGE_BF16) return fail(SAGE_ERR_INVALID, "bad dtype");
+  if (d->num_tables < 1 || d->num_tables > kMaxTables || !d->rows) return fail(SAGE_ERR_INVALID, "bad num_tables");
+  const int es = d->dtype == SAGE_BF16 ? 2 : 4;
+  const int rb = d->dim * es;
+  if (d->dim < 1 || rb < 16 || rb > 1024 || (rb & (rb - 1)))
+    return fail(SAGE_ERR_INVALID, "dim*elem must be a power of two in [16, 1024] bytes");
+  if (d->n_dense < 1 || d->n_dense > 64) return fail(SAGE_ERR_INVALID, "n_dense must be in [1, 64]");
+  if (d->n_bot < 1 || d->n_bot > 8 || d->n_top < 1 || d->n_top > 8 || !d->bot_dims || !d->top_dims)
+    return fail(SAGE_ERR_INVALID, "n_bot/n_top must be in [1, 8]");
+  if (d->top_dims[d->n_top - 1] != 1) return fail(SAGE_ERR_INVALID, "the last top layer must have 1 output");
+  size_t tb = 0;
+  for (int t = 0; t < d->num_tables; ++t) {
+    if (d->rows[t] < 1 || d->rows[t] >= (int64_t(1) << 31)) return fail(SAGE_ERR_INVALID, "bad rows[%d]", t);
+    tb += static_cast<size_t>(d->rows[t]) * d->dim * es;
+  }
+  if (d->tables.bytes != tb) return fail(SAGE_ERR_INVALID, "tables.bytes %zu != %zu", d->tables.bytes, tb);
+  if (d->tables.access != SAGE_READONLY || d->weights.access != SAGE_READONLY)
+    return fail(SAGE_ERR_INVALID, "tables and weights must be SAGE_READONLY");
+  if ((!d->tables.host_src) == (!d->tables.fill) || (!d->weights.host_src) == (!d->weights.fill))
+    return fail(SAGE_ERR_INVALID, "each data item needs exactly one of host_src or fill");
+  // layer shapes
+  std::vector<std::pair<int, int>> L;
+  int prev = d->n_dense;
+  for (int l = 0; l < d->n_bot; ++l) {
+    if (d->bot_dims[l] < 1) return fail(SAGE_ERR_INVALID, "bad bot_dims");
+    L.push_back({prev, d->bot_dims[l]});
+    prev = d->bot_dims[l];
+  }
+  prev = d->num_tables * d->dim + d->bot_dims[d->n_bot - 1];
+  for (int l = 0; l < d->n_top; ++l) {
+    if (d->top_dims[l] < 1) return fail(SAGE_ERR_INVALID, "bad top_dims");
+    L.push_back({prev, d->top_dims[l]});
+    prev = d->top_dims[l];
+  }
+  size_t wb = 0;
+  for (auto& p : L) {
+    wb = align256(wb) + static_cast<size_t>(p.first) * p.second * es;
+    wb = align256(wb) + static_cast<size_t>(p.second) * 4;
+  }
+  wb = align256(wb);
+  if (d->weights.bytes != wb) return fail(SAGE_ERR_INVALID, "weights.bytes %zu != %zu", d->weights.bytes, wb);
+  for (size_t l = 1; l + 1 < L.size(); ++l) {
+    const int K = L[l].first, N = L[l].second;
+    if (d->dtype == SAGE_BF16 && ((K % 64) || (N % 64)))
+      return fail(SAGE_ERR_INVALID, "bf16 layer %zu (%d -> %d) needs multiples of 64", l, K, N);
+    if (d->dtype == SAGE_F32 && ((K % 4) || (N % 4)))
+      return fail(SAGE_ERR_INVALID, "fp32 layer %zu (%d -> %d) needs multiples of 4", l, K, N);
+  }
+  if (d->dtype == SAGE_BF16 && d->n_bot == 1 && ((d->num_tables * d->dim) % 8))
+    return fail(SAGE_ERR_INVALID, "bad concat alignment");
+  if (d->max_batch < 0 || d->workspace_slots < 0 || d->workspace_slots > 64)
+    return fail(SAGE_ERR_INVALID, "bad max_batch/workspace_slots");
+  return SAGE_OK;
+}
+
+bool same_shape(const Entry* e, const sage_fn_desc* d) {
+  if (e->dtype != d->dtype || e->T != d->num_tables || e->dim != d->dim || e->n_dense != d->n_dense) return false;
+  if (static_cast<int>(e->bot.size()) != d->n_bot || static_cast<int>(e->top.size()) != d->n_top) return false;
+  for (int t = 0; t < e->T; ++t)
+    if (e->rows[t] != d->rows[t]) return false;
+  for (int l = 0; l < d->n_bot; ++l)
+    if (e->bot[l] != d->bot_dims[l]) return false;
+  for (int l = 0; l < d->n_top; ++l)
+    if (e->top[l] != d->top_dims[l]) return false;
+  return e->tables_bytes == d->tables.bytes && e->weights_bytes == d->weights.bytes;
+}
+
+// Free an entry's device memory after all of its work finished.
+void destroy_entry(sage_pool_s* P, Entry* e) {
+  {
+    std::unique_lock<std::mutex> l(e->smu);
+    e->cancel = true;
+    e->scv.wait(l, [&] { return e->sstate != 0; });
+  }
+  if (e->ready) cudaEventSynchronize(e->ready);
+  for (auto& s : e->slots) {
+    if (s.done) {
+      cudaEventSynchronize(s.done);
+      cudaEventDestroy(s.done);
+    }
+  }
+  cudaStreamSynchronize(P->side);
+  for (auto& s : e->slots) {
+    P->dev_free(s.buf, s.bytes, P->side);
+    P->dev_free(s.io, s.io_bytes, P->side);
+  }
+  P->dev_free(e->d_tables, e->tables_bytes, P->side);
+  P->dev_free(e->d_weights, e->weights_bytes, P->side);
+  P->dev_free(e->d_err, 256, P->side);
+  cudaStreamSynchronize(P->side);
+  if (e->ready) cudaEventDestroy(e->ready);
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    P->used -= e->reserved;
+  }
+  delete e;
+}
+
+// Wait (host) until the entry's setup finished and all staging copies are queued.
+sage_status wait_ready_enqueued(Entry* e) {
+  std::unique_lock<std::mutex> l(e->smu);
+  e->scv.wait(l, [&] { return e->sstate != 0 && e->setup != 0; });
+  if (e->sstate == 2) return fail(SAGE_ERR_STAGING, "staging of '%s' failed", e->key.c_str());
+  if (e->setup == 2) return fail(SAGE_ERR_CUDA, "setup of '%s' failed", e->key.c_str());
+  return SAGE_OK;
+}
+
+bool valid_fn(sage_fn f) { return f && f->magic == kFnMagic && f->e; }
+
+sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t stream) {
+  const int M = tab.M;
+  const int nb = static_cast<int>(e->bot.size()), nt = static_cast<int>(e->top.size());
+  const size_t es = e->elem();
+  const int cd = e->concat_dim();
+  char* bot_out = s.concat + static_cast<size_t>(e->T) * e->dim * es;
+  // bottom MLP (layer 0 reads each invocation's dense rows)
+  {
+    const Layer& L0 = e->layers[0];
+    void* y = nb == 1 ? bot_out : s.bot[0];
+    const int ldy = nb == 1 ? cd : e->bot[0];
+    SAGE_CK(launch_bottom0(e->dtype, tab, L0.in, L0.out, L0.W, L0.b, y, ldy, stream));
+  }
+  for (int l = 1; l < nb; ++l) {
+    const Layer& L = e->layers[l];
+    const void* x = s.bot[l - 1];
+    void* y = l == nb - 1 ? bot_out : s.bot[l];
+    const int ldy = l == nb - 1 ? cd : e->bot[l];
+    if (e->dtype == SAGE_BF16)
+      SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, L.in, L.W, L.b, 1, y, ldy, e->d_err, stream));
+    else
+      SAGE_CK(launch_linear_f32(M, L.out, L.in, static_cast<const float*>(x), L.in, static_cast<const float*>(L.W),
+                                L.b, 1, static_cast<float*>(y), ldy, stream));
+  }
+  // embedding-bag gather into the concat columns [0, T*dim)
+  {
+    GatherArgs a;
+    a.dtype = e->dtype;
+    a.tables = e->d_tables;
+    for (int t = 0; t < e->T; ++t) {
+      a.table_off[t] = e->table_off[t];
+      a.table_rows[t] = static_cast<int32_t>(e->rows[t]);
+    }
+    a.T = e->T;
+    a.dim = e->dim;
+    a.out = s.concat;
+    a.ldo = cd;
+    a.err = e->d_err;
+    SAGE_CK(launch_gather(a, tab, stream));
+  }
+  // top MLP hidden layers
+  const char* x = s.concat;
+  int ldx = cd;
+  for (int l = 0; l + 1 < nt; ++l) {
+    const Layer& L = e->layers[nb + l];
+    char* y = s.top[l];
+    if (e->dtype == SAGE_BF16)
+      SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, ldx, L.W, L.b, 1, y, L.out, e->d_err, stream));
+    else
+      SAGE_CK(launch_linear_f32(M, L.out, L.in, reinterpret_cast<const float*>(x), ldx,
+                                static_cast<const float*>(L.W), L.b, 1, reinterpret_cast<float*>(y), L.out,
+                                stream));
+    x = y;
+    ldx = L.out;
+  }
+  // sigmoid head, written to each invocation's out
+  const Layer& H = e->layers[nb + nt - 1];
+  SAGE_CK(launch_head(e->dtype, tab, H.in, x, ldx, H.W, H.b, stream));
+  return SAGE_OK;
+}
+
+// Pick a slot able to hold M rows; called with e->imu held.
+sage_status acquire_slot(Entry* e, int M, cudaStream_t stream, Slot** out) {
+  Slot& s = e->slots[e->next_slot];
+  e->next_slot = (e->next_slot + 1) % static_cast<int>(e->slots.size());
+  if (s.used) SAGE_CK(cudaStreamWaitEvent(stream, s.done, 0));
+  if (M > s.cap) {
+    // grow: wait for the slot's last use, then reallocate (rare)
+    if (s.used) SAGE_CK(cudaEventSynchronize(s.done));
+    int cap = std::max(M, s.cap + s.cap / 2);
+    const size_t old_bytes = s.bytes;
+    const size_t need = slot_bytes(e, cap);
+    {
+      std::lock_guard<std::mutex> g(e->pool->mu);
+      if (need > old_bytes && e->pool->used + (need - old_bytes) > e->pool->budget)
+        return fail(SAGE_ERR_NOMEM, "workspace growth to %d rows exceeds the pool budget", cap);
+      if (need > old_bytes) {
+        e->pool->used += need - old_bytes;
+        e->reserved += need - old_bytes;
+      }
+    }
+    sage_status st = build_slot(e, s, cap, stream);
+    if (st != SAGE_OK) return st;
+  }
+  *out = &s;
+  return SAGE_OK;
+}
+
+sage_status run_batch(Entry* e, const InvTable& tab, cudaStream_t stream) {
+  std::lock_guard<std::mutex> g(e->imu);
+  Slot* s = nullptr;
+  sage_status st = acquire_slot(e, tab.M, stream, &s);
+  if (st != SAGE_OK) return st;
+  SAGE_CK(cudaStreamWaitEvent(stream, e->ready, 0));
+  st = launch_chain(e, *s, tab, stream);
+  if (st != SAGE_OK) return st;
+  SAGE_CK(cudaEventRecord(s->done, stream));
+  s->used = true;
+  return SAGE_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+
+extern "C" {
+
+const char* sage_last_error(void) { return t_err.c_str(); }
+
+int64_t sage_kernel_launches(void) { return sage::launches(); }
+
+sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
+  if (!out) return fail(SAGE_ERR_INVALID, "null out");
+  *out = nullptr;
+  sage_pool_config c{};
+  if (cfg) c = *cfg;
+  if ((c.dev_alloc == nullptr) != (c.dev_free == nullptr))
+    return fail(SAGE_ERR_INVALID, "set both dev_alloc and dev_free or neither");
+  auto t0 = Clock::now();
+  SAGE_CK(cudaSetDevice(c.device));
+  SAGE_CK(cudaFree(nullptr));  // create / bind the context
+  std::unique_ptr<sage_pool_s> P(new sage_pool_s());
+  P->device = c.device;
+  P->dalloc = c.dev_alloc;
+  P->dfree = c.dev_free;
+  P->actx = c.alloc_ctx;
+  P->serial_setup = c.serial_setup != 0;
+  size_t free_b = 0, total_b = 0;
+  SAGE_CK(cudaMemGetInfo(&free_b, &total_b));
+  const size_t margin = size_t(2) << 30;
+  P->budget = c.budget_bytes ? c.budget_bytes : (free_b > margin ? free_b - margin : free_b / 2);
+  P->chunk_bytes = c.staging_chunk_bytes ? ((c.staging_chunk_bytes + 4095) & ~size_t(4095)) : (size_t(64) << 20);
+  const int nchunks = c.staging_chunks > 0 ? c.staging_chunks : 4;
+  SAGE_CK(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+  for (int i = 0; i < nchunks; ++i) {
+    void* h = nullptr;
+    SAGE_CK(cudaHostAlloc(&h, P->chunk_bytes, cudaHostAllocDefault));
+    P->ring.push_back(static_cast<char*>(h));
+    cudaEvent_t ev;
+    SAGE_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SAGE_CK(cudaEventRecord(ev, P->side));
+    P->ring_ev.push_back(ev);
+  }
+  int hw = static_cast<int>(std::thread::hardware_concurrency());
+  int nthreads = c.producer_threads > 0 ? c.producer_threads : std::min(16, std::max(1, hw));
+  P->workers.reset(new Workers(std::max(0, nthreads - 1)));
+  sage_pool_s* raw = P.get();
+  P->stager = std::thread([raw] { stager_loop(raw); });
+  P->st.ctx_ms = ms_since(t0);
+  *out = P.release();
+  return SAGE_OK;
+}
+
+sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
+  if (!P || !out) return fail(SAGE_ERR_INVALID, "null pool or out");
+  *out = nullptr;
+  sage_status st = check_desc(d);
+  if (st != SAGE_OK) return st;
+  auto t0 = Clock::now();
+  SAGE_CK(cudaSetDevice(P->device));
+  Entry* e = nullptr;
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    P->st.prepares++;
+    auto it = P->entries.find(d->fn_key);
+    if (it != P->entries.end()) {
+      // read-only sharing: take a reference, load nothing
+      if (!same_shape(it->second, d))
+        return fail(SAGE_ERR_INVALID, "key '%s' is resident with another shape", d->fn_key);
+      it->second->refs++;
+      P->st.hits++;
+      sage_fn f = new sage_fn_s{P, it->second, kFnMagic};
+      P->handles.insert(f);
+      *out = f;
+      P->st.last_prepare_ms = ms_since(t0);
+      return SAGE_OK;
+    }
+    e = new Entry();
+    e->pool = P;
+    e->key = d->fn_key;
+    e->dtype = d->dtype;
+    e->T = d->num_tables;
+    e->dim = d->dim;
+    e->n_dense = d->n_dense;
+    e->rows.assign(d->rows, d->rows + d->num_tables);
+    e->bot.assign(d->bot_dims, d->bot_dims + d->n_bot);
+    e->top.assign(d->top_dims, d->top_dims + d->n_top);
+    e->tables_bytes = d->tables.bytes;
+    e->weights_bytes = d->weights.bytes;
+    e->tdesc = d->tables;
+    e->wdesc = d->weights;
+    e->max_batch = d->max_batch > 0 ? d->max_batch : 4096;
+    const int nslots = d->workspace_slots > 0 ? d->workspace_slots : 2;
+    e->slots.resize(nslots);
+    e->ws_bytes = static_cast<size_t>(nslots) * slot_bytes(e, e->max_batch);
+    const size_t need = align256(e->tables_bytes) + align256(e->weights_bytes) + e->ws_bytes + 256;
+    if (P->used + need > P->budget) {
+      delete e;
+      return fail(SAGE_ERR_NOMEM, "prepare of '%s' needs %zu bytes; %zu of %zu in use", d->fn_key, need, P->used,
+                  P->budget);
+    }
+    P->used += need;
+    e->reserved = need;
+    e->refs = 1;
+    e->t_prepare = t0;
+    P->entries[e->key] = e;
+    P->st.misses++;
+  }
+  auto setup_failed = [&](sage_status s2) {
+    std::string msg = t_err;
+    {
+      std::lock_guard<std::mutex> g(e->smu);
+      e->setup = 2;
+      if (!e->queued) e->sstate = 2;
+      e->scv.notify_all();
+    }
+    bool last = false;
+    {
+      std::lock_guard<std::mutex> g(P->mu);
+      auto it = P->entries.find(e->key);
+      if (it != P->entries.end() && it->second == e) P->entries.erase(it);
+      last = --e->refs == 0;
+    }
+    if (last) destroy_entry(P, e);
+    t_err = msg;
+    return s2;
+  };
+
+  // read-only copy and the staging job (returns at once)
+  cudaError_t ce = cudaEventCreateWithFlags(&e->ready, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    e->ready = nullptr;
+    return setup_failed(fail(SAGE_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce)));
+  }
+  e->d_tables = static_cast<char*>(P->dev_alloc(e->tables_bytes, P->side));
+  e->d_weights = static_cast<char*>(P->dev_alloc(e->weights_bytes, P->side));
+  if (!e->d_tables || !e->d_weights)
+    return setup_failed(fail(SAGE_ERR_NOMEM, "device allocation of the read-only data of '%s' failed", d->fn_key));
+  {
+    int64_t o = 0;
+    for (int t = 0; t < e->T; ++t) {
+      e->table_off[t] = o;
+      o += e->rows[t] * e->dim * static_cast<int64_t>(e->elem());
+    }
+  }
+  {
+    std::lock_guard<std::mutex> g(e->smu);
+    e->queued = true;
+  }
+  {
+    std::lock_guard<std::mutex> g(P->qmu);
+    P->queue.push_back(e);
+  }
+  P->qcv.notify_one();
+  if (P->serial_setup) {
+    std::unique_lock<std::mutex> l(e->smu);
+    e->scv.wait(l, [&] { return e->sstate != 0; });
+    l.unlock();
+    cudaEventSynchronize(e->ready);
+  }
+
+  // meanwhile on this thread: kernels (module load) and workspace
+  auto tm = Clock::now();
+  load_kernels_once();
+  const double module_ms = ms_since(tm);
+  auto tw = Clock::now();
+  {
+    // layer pointers inside the weights item
+    size_t o = 0;
+    int prev = e->n_dense;
+    std::vector<std::pair<int, int>> L;
+    for (int v : e->bot) {
+      L.push_back({prev, v});
+      prev = v;
+    }
+    prev = e->concat_dim();
+    for (int v : e->top) {
+      L.push_back({prev, v});
+      prev = v;
+    }
+    for (auto& p : L) {
+      o = align256(o);
+      const void* W = e->d_weights + o;
+      o += static_cast<size_t>(p.first) * p.second * e->elem();
+      o = align256(o);
+      const float* b = reinterpret_cast<const float*>(e->d_weights + o);
+      o += static_cast<size_t>(p.second) * 4;
+      e->layers.push_back({p.first, p.second, W, b});
+    }
+  }
+  e->d_err = static_cast<int*>(P->dev_alloc(256, P->side));
+  if (!e->d_err) return setup_failed(fail(SAGE_ERR_NOMEM, "error word allocation failed"));
+  ce = cudaMemsetAsync(e->d_err, 0, 256, P->side);
+  if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "memset: %s", cudaGetErrorString(ce)));
+  for (auto& s : e->slots) {
+    st = build_slot(e, s, e->max_batch, P->side);
+    if (st != SAGE_OK) return setup_failed(st);
+    ce = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "event: %s", cudaGetErrorString(ce)));
+  }
+  // allocations on the side stream must precede any use on other streams
+  ce = cudaEventRecord(e->slots[0].done, P->side);
+  if (ce == cudaSuccess) ce = cudaEventSynchronize(e->slots[0].done);
+  if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "setup sync: %s", cudaGetErrorString(ce)));
+  const double ws_ms = ms_since(tw);
+  {
+    std::lock_guard<std::mutex> g(e->smu);
+    e->setup = 1;
+    e->scv.notify_all();
+  }
+  sage_fn f = new sage_fn_s{P, e, kFnMagic};
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    P->handles.insert(f);
+    P->st.last_module_ms = module_ms;
+    P->st.last_workspace_ms = ws_ms;
+    P->st.last_prepare_ms = ms_since(t0);
+  }
+  *out = f;
+  return SAGE_OK;
+}
+
+sage_status sage_fn_query(sage_fn f) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  Entry* e = f->e;
+  std::unique_lock<std::mutex> l(e->smu);
+  if (e->sstate == 2) return fail(SAGE_ERR_STAGING, "staging of '%s' failed", e->key.c_str());
+  if (e->sstate == 0 || e->setup == 0) return SAGE_PENDING;
+  cudaEvent_t ev = e->ready;
+  l.unlock();
+  cudaError_t q = cudaEventQuery(ev);
+  if (q == cudaSuccess) return SAGE_OK;
+  if (q == cudaErrorNotReady) {
+    cudaGetLastError();
+    return SAGE_PENDING;
+  }
+  return fail(SAGE_ERR_CUDA, "cudaEventQuery: %s", cudaGetErrorString(q));
+}
+
+sage_status sage_fn_wait(sage_fn f, int64_t timeout_us) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  auto t0 = Clock::now();
+  for (;;) {
+    sage_status st = sage_fn_query(f);
+    if (st != SAGE_PENDING) return st;
+    if (timeout_us >= 0 &&
+        std::chrono::duration<double, std::micro>(Clock::now() - t0).count() > static_cast<double>(timeout_us))
+      return fail(SAGE_ERR_TIMEOUT, "staging of '%s' not finished within %lld us", f->e->key.c_str(),
+                  static_cast<long long>(timeout_us));
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+sage_status sage_invoke_batch(sage_fn f, const sage_invocation* invs, int n, void* stream) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  if (n < 0 || (n > 0 && !invs)) return fail(SAGE_ERR_INVALID, "bad invocation list");
+  Entry* e = f->e;
+  sage_status st = wait_ready_enqueued(e);
+  if (st != SAGE_OK) return st;
+  SAGE_CK(cudaSetDevice(e->pool->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::unique_ptr<InvTable> tab(new InvTable());
+  int i = 0;
+  while (i < n) {
+    tab->n = 0;
+    int64_t M = 0;
+    while (i < n && tab->n < kMaxInv) {
+      const sage_invocation& v = invs[i];
+      if (v.batch < 0) return fail(SAGE_ERR_INVALID, "invocation %d: negative batch", i);
+      if (v.batch > 0 && (!v.dense || !v.indices || !v.offsets || !v.out))
+        return fail(SAGE_ERR_INVALID, "invocation %d: null buffer", i);
+      if (M + v.batch > (int64_t(1) << 30)) return fail(SAGE_ERR_INVALID, "batch too large (over 2^30 rows)");
+      if (v.batch > 0) {
+        InvDesc& dd = tab->d[tab->n++];
+        dd.dense = v.dense;
+        dd.indices = v.indices;
+        dd.offsets = v.offsets;
+        dd.out = v.out;
+        dd.batch = v.batch;
+        dd.row_base = static_cast<int>(M);
+        M += v.batch;
+      }
+      ++i;
+    }
+    tab->M = static_cast<int>(M);
+    if (tab->n == 0) continue;
+    st = run_batch(e, *tab, s);
+    if (st != SAGE_OK) return st;
+    e->pool->invocations += tab->n;
+  }
+  return SAGE_OK;
+}
+
+sage_status sage_invoke(sage_fn f, const sage_invocation* inv, void* stream) {
+  if (!inv) return fail(SAGE_ERR_INVALID, "null invocation");
+  return sage_invoke_batch(f, inv, 1, stream);
+}
+
+sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, int n, void* stream) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  if (n < 0 || (n > 0 && !invs)) return fail(SAGE_ERR_INVALID, "bad invocation list");
+  if (n > kMaxInv) {
+    for (int i = 0; i < n; i += kMaxInv) {
+      sage_status st = sage_invoke_batch_host(f, invs + i, std::min(kMaxInv, n - i), stream);
+      if (st != SAGE_OK) return st;
+    }
+    return SAGE_OK;
+  }
+  Entry* e = f->e;
+  sage_status st = wait_ready_enqueued(e);
+  if (st != SAGE_OK) return st;
+  SAGE_CK(cudaSetDevice(e->pool->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // arena regions: dense | indices | offsets | out, each invocation's part 256-aligned
+  size_t nd = 0, ni = 0, no = 0, nu = 0;
+  int64_t M = 0;
+  for (int i = 0; i < n; ++i) {
+    const sage_host_invocation& v = invs[i];
+    if (v.batch < 0 || v.num_indices < 0) return fail(SAGE_ERR_INVALID, "invocation %d: bad sizes", i);
+    if (v.batch == 0) continue;
+    if (!v.dense || !v.offsets || !v.out || (v.num_indices > 0 && !v.indices))
+      return fail(SAGE_ERR_INVALID, "invocation %d: null buffer", i);
+    nd += static_cast<size_t>(v.batch) * e->n_dense * 4;
+    ni += static_cast<size_t>(v.num_indices) * 4;
+    no += (static_cast<size_t>(e->T) * v.batch + 1) * 8;
+    nu += static_cast<size_t>(v.batch) * 4;
+    M += v.batch;
+  }
+  if (M == 0) return SAGE_OK;
+  const size_t need = align256(nd) + align256(ni) + align256(no) + align256(nu);
+  std::unique_ptr<InvTable> tab(new InvTable());
+  {
+    std::lock_guard<std::mutex> g(e->imu);
+    Slot* sl = nullptr;
+    st = acquire_slot(e, static_cast<int>(M), s, &sl);
+    if (st != SAGE_OK) return st;
+    if (sl->io_bytes < need) {
+      if (sl->used) SAGE_CK(cudaEventSynchronize(sl->done));
+      e->pool->dev_free(sl->io, sl->io_bytes, s);
+      const size_t nb = need + need / 4;
+      sl->io = static_cast<char*>(e->pool->dev_alloc(nb, s));
+      sl->io_bytes = sl->io ? nb : 0;
+      if (!sl->io) return fail(SAGE_ERR_NOMEM, "host-invocation arena of %zu bytes", nb);
+    }
+    char* pd = sl->io;
+    char* pi = pd + align256(nd);
+    char* po = pi + align256(ni);
+    char* pu = po + align256(no);
+    // H2D copies; adjacent host ranges are merged into one copy
+    struct Run {
+      char* dst;
+      const char* src;
+      size_t n;
+    };
+    std::vector<Run> runs;
+    auto add = [&](char* dst, const void* src, size_t nbytes) {
+      if (nbytes == 0) return;
+      if (!runs.empty() && runs.back().dst + runs.back().n == dst &&
+          runs.back().src + runs.back().n == static_cast<const char*>(src)) {
+        runs.back().n += nbytes;
+      } else {
+        runs.push_back({dst, static_cast<const char*>(src), nbytes});
+      }
+    };
+    tab->n = 0;
+    int64_t row = 0;
+    std::vector<Run> dense_r, idx_r, off_r;
+    size_t od = 0, oi = 0, oo = 0, ou = 0;
+    for (int i = 0; i < n; ++i) {
+      const sage_host_invocation& v = invs[i];
+      if (v.batch == 0) continue;
+      const size_t bd = static_cast<size_t>(v.batch) * e->n_dense * 4;
+      const size_t bi = static_cast<size_t>(v.num_indices) * 4;
+      const size_t bo = (static_cast<size_t>(e->T) * v.batch + 1) * 8;
+      InvDesc& dd = tab->d[tab->n++];
+      dd.dense = reinterpret_cast<const float*>(pd + od);
+      dd.indices = reinterpret_cast<const int32_t*>(pi + oi);
+      dd.offsets = reinterpret_cast<const int64_t*>(po + oo);
+      dd.out = reinterpret_cast<float*>(pu + ou);
+      dd.batch = v.batch;
+      dd.row_base = static_cast<int>(row);
+      dense_r.push_back({pd + od, reinterpret_cast<const char*>(v.dense), bd});
+      idx_r.push_back({pi + oi, reinterpret_cast<const char*>(v.indices), bi});
+      off_r.push_back({po + oo, reinterpret_cast<const char*>(v.offsets), bo});
+      od += bd;
+      oi += bi;
+      oo += bo;
+      ou += static_cast<size_t>(v.batch) * 4;
+      row += v.batch;
+    }
+    tab->M = static_cast<int>(row);
+    for (auto& r : dense_r) add(r.dst, r.src, r.n);
+    for (auto& r : idx_r) add(r.dst, r.src, r.n);
+    for (auto& r : off_r) add(r.dst, r.src, r.n);
+    for (auto& r : runs) SAGE_CK(cudaMemcpyAsync(r.dst, r.src, r.n, cudaMemcpyHostToDevice, s));
+    SAGE_CK(cudaStreamWaitEvent(s, e->ready, 0));
+    st = launch_chain(e, *sl, *tab, s);
+    if (st != SAGE_OK) return st;
+    // D2H of the outputs, merged where the host outputs are adjacent
+    runs.clear();
+    size_t ou2 = 0;
+    for (int i = 0; i < n; ++i) {
+      const sage_host_invocation& v = invs[i];
+      if (v.batch == 0) continue;
+      const size_t bu = static_cast<size_t>(v.batch) * 4;
+      char* hdst = reinterpret_cast<char*>(v.out);
+      if (!runs.empty() && const_cast<char*>(runs.back().src) + runs.back().n == pu + ou2 &&
+          runs.back().dst + runs.back().n == hdst) {
+        runs.back().n += bu;
+      } else {
+        runs.push_back({hdst, pu + ou2, bu});
+      }
+      ou2 += bu;
+    }
+    for (auto& r : runs) SAGE_CK(cudaMemcpyAsync(r.dst, r.src, r.n, cudaMemcpyDeviceToHost, s));
+    SAGE_CK(cudaEventRecord(sl->done, s));
+    sl->used = true;
+  }
+  e->pool->invocations += n;
+  SAGE_CK(cudaStreamSynchronize(s));
+  return SAGE_OK;
+}
+
+sage_status sage_fn_check(sage_fn f) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  Entry* e = f->e;
+  sage_status st = wait_ready_enqueued(e);
+  if (st != SAGE_OK) return st;
+  SAGE_CK(cudaSetDevice(e->pool->device));
+  {
+    std::lock_guard<std::mutex> g(e->imu);
+    for (auto& s : e->slots)
+      if (s.used) SAGE_CK(cudaEventSynchronize(s.done));
+  }
+  int w = 0;
+  SAGE_CK(cudaMemcpy(&w, e->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  SAGE_CK(cudaMemset(e->d_err, 0, sizeof(int)));
+  if (w & kErrTimeout) return fail(SAGE_ERR_DEVICE, "a kernel's bounded wait ran out");
+  if (w & kErrBounds) return fail(SAGE_ERR_BOUNDS, "a bag row index was outside its table");
+  return SAGE_OK;
+}
+
+sage_status sage_release(sage_fn f) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  sage_pool_s* P = f->pool;
+  Entry* e = nullptr;
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    auto it = P->handles.find(f);
+    if (it == P->handles.end()) return fail(SAGE_ERR_INVALID, "handle already released");
+    P->handles.erase(it);
+    f->magic = 0;
+    if (--f->e->refs == 0) {
+      e = f->e;
+      auto ie = P->entries.find(e->key);
+      if (ie != P->entries.end() && ie->second == e) P->entries.erase(ie);
+    }
+  }
+  delete f;
+  if (e) {
+    SAGE_CK(cudaSetDevice(P->device));
+    destroy_entry(P, e);
+  }
+  return SAGE_OK;
+}
+
+sage_status sage_pool_destroy(sage_pool P) {
+  if (!P) return fail(SAGE_ERR_INVALID, "null pool");
+  {
+    std::lock_guard<std::mutex> g(P->mu);
+    if (!P->handles.empty()) return fail(SAGE_ERR_BUSY, "%zu function handles are live", P->handles.size());
+  }
+  {
+    std::lock_guard<std::mutex> g(P->qmu);
+    P->stop = true;
+  }
+  P->qcv.notify_all();
+  if (P->stager.joinable()) P->stager.join();
+  cudaSetDevice(P->device);
+  cudaStreamSynchronize(P->side);
+  for (size_t i = 0; i < P->ring.size(); ++i) {
+    cudaEventDestroy(P->ring_ev[i]);
+    cudaFreeHost(P->ring[i]);
+  }
+  cudaStreamDestroy(P->side);
+  P->workers.reset();
+  delete P;
+  return SAGE_OK;
+}
+
+sage_status sage_pool_stats_get(sage_pool P, sage_pool_stats* out) {
+  if (!P || !out) return fail(SAGE_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> g(P->mu);
+  sage_pool_stats s = P->st;
+  s.budget_bytes = P->budget;
+  s.resident_bytes = P->used;
+  s.readonly_bytes = 0;
+  s.functions = static_cast<int64_t>(P->entries.size());
+  s.refs = static_cast<int64_t>(P->handles.size());
+  for (auto& kv : P->entries) s.readonly_bytes += kv.second->tables_bytes + kv.second->weights_bytes;
+  s.h2d_bytes = P->h2d.load();
+  s.invocations = P->invocations.load();
+  s.launches = sage::launches();
+  *out = s;
+  return SAGE_OK;
+}
+
+// ---------------------------------------------------------------- building blocks
+
+sage_status sage_embedding_bag_sum(sage_dtype dtype, const void* tables, const int64_t* table_rows, int num_tables,
+                                   int dim, int batch, const int32_t* indices, const int64_t* offsets, void* out,
+                                   int ldo, int* err_word, void* stream) {
+  if (num_tables < 1 || num_tables > kMaxTables || !tables || !table_rows || batch < 0 || !out)
+    return fail(SAGE_ERR_INVALID, "bad embedding-bag arguments");
+  if (batch == 0) return SAGE_OK;
+  const int es = dtype == SAGE_BF16 ? 2 : 4;
+  if (ldo < num_tables * dim || ((static_cast<size_t>(ldo) * es) & 15) || (reinterpret_cast<uintptr_t>(out) & 15) ||
+      (reinterpret_cast<uintptr_t>(tables) & 15))
+    return fail(SAGE_ERR_INVALID, "ldo / alignment");
+  std::unique_ptr<InvTable> tab(new InvTable());
+  tab->n = 1;
+  tab->M = batch;
+  tab->d[0] = InvDesc{nullptr, indices, offsets, nullptr, batch, 0};
+  GatherArgs a;
+  a.dtype = dtype;
+  a.tables = static_cast<const char*>(tables);
+  int64_t o = 0;
+  for (int t = 0; t < num_tables; ++t) {
+    if (table_rows[t] < 1 || table_rows[t] >= (int64_t(1) << 31)) return fail(SAGE_ERR_INVALID, "bad table_rows");
+    a.table_off[t] = o;
+    a.table_rows[t] = static_cast<int32_t>(table_rows[t]);
+    o += table_rows[t] * dim * es;
+  }
+  a.T = num_tables;
+  a.dim = dim;
+  a.out = out;
+  a.ldo = ldo;
+  a.err = err_word;
+  cudaError_t e = launch_gather(a, *tab, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return fail(SAGE_ERR_INVALID, "unsupported dim");
+  SAGE_CK(e);
+  return SAGE_OK;
+}
+
+sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,
+                        const float* bias, int act, void* y, int ldy, int* err_word, void* stream) {
+  if (M < 0 || N < 1 || K < 1 || !x || !W || !bias || !y) return fail(SAGE_ERR_INVALID, "bad linear arguments");
+  cudaError_t e;
+  if (dtype == SAGE_BF16)
+    e = launch_linear_bf16_tc(M, N, K, x, ldx, W, bias, act, y, ldy, err_word, static_cast<cudaStream_t>(stream));
+  else
+    e = launch_linear_f32(M, N, K, static_cast<const float*>(x), ldx, static_cast<const float*>(W), bias, act,
+                          static_cast<float*>(y), ldy, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return fail(SAGE_ERR_INVALID, "unsupported shape or alignment");
+  SAGE_CK(e);
+  return SAGE_OK;
+}
+
+}  // extern "C"

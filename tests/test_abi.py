@@ -1,0 +1,89 @@
+"""The C-ABI library loads and exports every entry point include/sage.h declares (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sage.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:sage_status|const char\*|int64_t)\s+(sage_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def libsage():
+    from paper_2404_14691_b300 import build
+    build.build()
+    from paper_2404_14691_b300 import _native
+    return _native.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("sage_pool_create", "sage_prepare", "sage_invoke", "sage_invoke_batch", "sage_release",
+              "sage_pool_destroy", "sage_fn_wait", "sage_embedding_bag_sum", "sage_linear"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libsage):
+    for n in _declared():
+        assert hasattr(libsage, n), n
+        assert isinstance(getattr(libsage, n), ctypes._CFuncPtr)
+
+
+def test_binding_declares_signatures_for_every_symbol(libsage):
+    from paper_2404_14691_b300 import _native
+    bound = {name for name, _, _ in _native.SIGNATURES}
+    assert bound == set(_declared())
+
+
+def test_exported_symbols_are_c_linkage(libsage):
+    from paper_2404_14691_b300 import _native
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for n in _declared():
+        assert n in syms, n
+
+
+def test_ctypes_struct_sizes_match_the_header():
+    """Compile a tiny C program against include/sage.h and compare sizeof/offsetof."""
+    from paper_2404_14691_b300 import _native as N
+    prog = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "sage.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(sage_pool_config), sizeof(sage_data_desc), sizeof(sage_fn_desc),
+         sizeof(sage_invocation), sizeof(sage_host_invocation), sizeof(sage_pool_stats),
+         offsetof(sage_fn_desc, weights));
+  return 0;
+}
+'''
+    tmp = os.path.join("/tmp", "sage_abi_%d" % os.getpid())
+    with open(tmp + ".c", "w") as f:
+        f.write(prog)
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", tmp, tmp + ".c"])
+    got = [int(x) for x in subprocess.check_output([tmp]).split()]
+    want = [ctypes.sizeof(N.PoolConfig), ctypes.sizeof(N.DataDesc), ctypes.sizeof(N.FnDesc),
+            ctypes.sizeof(N.Invocation), ctypes.sizeof(N.HostInvocation), ctypes.sizeof(N.PoolStats),
+            N.FnDesc.weights.offset]
+    assert got == want
+    os.remove(tmp)
+    os.remove(tmp + ".c")
+
+
+def test_calls_without_gpu_fail_cleanly(libsage):
+    """With no GPU visible, pool creation returns an error status (no crash)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is visible")
+    h = ctypes.c_void_p()
+    st = libsage.sage_pool_create(None, ctypes.byref(h))
+    assert st == -3
+    assert libsage.sage_last_error()

@@ -1,0 +1,286 @@
+"""The runtime through the C-ABI on a GPU: whole function vs the oracle, fused
+batches vs isolated invocations, read-only sharing and refcounts, staging
+failures, budget, readiness gate, host-buffer invocations, concurrency."""
+import ctypes
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from helpers import RTOL, DevInvocation, oracle_rows, prepare, to_f64
+
+pytestmark = pytest.mark.gpu
+
+sage = pytest.importorskip("paper_2404_14691_b300")
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def spec_small(dtype, key=None):
+    if dtype == "f32":
+        return workload.spec_tiny(key=key or "rt_f32", dtype="f32", n_tables=4, rows=2000, dim=32,
+                                  bot=(64, 32), top=(64, 32, 1), l_min=0, l_max=30)
+    return workload.FunctionSpec(key=key or "rt_bf16", dtype="bf16", rows=[3000, 2000, 5000], dim=64,
+                                 bot_dims=[128, 64], top_dims=[128, 64, 1], alpha=1.1, l_min=0, l_max=40)
+
+
+@pytest.fixture(scope="module")
+def pool():
+    p = sage.Pool(device=0, staging_chunk_bytes=1 << 20, staging_chunks=3)
+    yield p
+    p.destroy()
+
+
+def _check_inv(spec, weights, dinv, rtol):
+    _torch().cuda.synchronize()
+    got = to_f64(dinv.out)[:dinv.batch]
+    tables = [workload.full_table(spec, t) for t in range(spec.n_tables)]
+    res = oracle.forward(spec, weights, dinv.inv, tables=tables, want_pooled=False)
+    c = oracle.check_close(got, res["out"], res["out_mag"], rtol)
+    assert c["ok"], c
+    return c
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_invoke_matches_oracle(pool, dtype):
+    spec = spec_small(dtype)
+    fn = prepare(pool, spec)
+    try:
+        w = workload.weights_arrays(spec)
+        for B, seed in [(1, 1), (37, 2), (300, 3)]:
+            d = DevInvocation(workload.make_invocation(spec, B, seed=seed))
+            fn.invoke(*d.args())
+            _check_inv(spec, w, d, RTOL[dtype])
+        fn.check_errors()
+    finally:
+        fn.release()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_fused_batch_equals_isolated_bitwise(pool, dtype):
+    torch = _torch()
+    spec = spec_small(dtype, key="rt_fuse_" + dtype)
+    fn = prepare(pool, spec)
+    try:
+        sizes = [5, 1, 130, 0, 77, 260]
+        invs = [workload.make_invocation(spec, B, seed=100 + i) for i, B in enumerate(sizes)]
+        fused = [DevInvocation(v) for v in invs]
+        alone = [DevInvocation(v) for v in invs]
+        fn.invoke_batch([d.args() for d in fused])
+        for d in alone:
+            fn.invoke(*d.args())
+        torch.cuda.synchronize()
+        w = workload.weights_arrays(spec)
+        for a, b in zip(fused, alone):
+            assert torch.equal(a.out[:a.batch], b.out[:b.batch])
+            if a.batch:
+                _check_inv(spec, w, a, RTOL[dtype])
+    finally:
+        fn.release()
+
+
+def test_host_buffer_invocation_equals_device_invocation(pool):
+    torch = _torch()
+    spec = spec_small("bf16", key="rt_host")
+    fn = prepare(pool, spec)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=200 + i) for i, B in enumerate([3, 64, 17])]
+        hosts = []
+        outs = []
+        for v in invs:
+            o = np.full(v["batch"], np.nan, np.float32)
+            outs.append(o)
+            hosts.append((v["batch"], v["dense"].ctypes.data, v["indices"].ctypes.data, v["offsets"].ctypes.data,
+                          v["indices"].size, o.ctypes.data))
+        fn.invoke_batch_host(hosts)
+        devs = [DevInvocation(v) for v in invs]
+        fn.invoke_batch([d.args() for d in devs])
+        torch.cuda.synchronize()
+        for o, d in zip(outs, devs):
+            assert np.array_equal(o, d.out[:d.batch].cpu().numpy())
+    finally:
+        fn.release()
+
+
+def test_readonly_sharing_loads_once_and_refcounts_free(pool):
+    spec = spec_small("f32", key="rt_share")
+    s0 = pool.stats()
+    f1 = prepare(pool, spec)
+    f2 = prepare(pool, spec)
+    f3 = prepare(pool, spec)
+    f1.wait()
+    s1 = pool.stats()
+    wbytes = workload.weights_blob(spec).nbytes
+    assert s1["h2d_bytes"] - s0["h2d_bytes"] == spec.table_bytes() + wbytes
+    assert s1["hits"] - s0["hits"] == 2 and s1["misses"] - s0["misses"] == 1
+    assert s1["functions"] == s0["functions"] + 1 and s1["refs"] == s0["refs"] + 3
+    # all three handles see the same results
+    d = [DevInvocation(workload.make_invocation(spec, 50, seed=9)) for _ in range(3)]
+    for f, x in zip((f1, f2, f3), d):
+        f.invoke(*x.args())
+    _torch().cuda.synchronize()
+    assert _torch().equal(d[0].out, d[1].out) and _torch().equal(d[0].out, d[2].out)
+    f1.release()
+    f2.release()
+    assert pool.stats()["functions"] == s0["functions"] + 1
+    f3.release()
+    s2 = pool.stats()
+    assert s2["functions"] == s0["functions"] and s2["resident_bytes"] == s0["resident_bytes"]
+    assert s2["refs"] == s0["refs"]
+    with pytest.raises(sage.SageError):
+        f3.handle = ctypes.c_void_p(0)
+        f3.release()
+
+
+def test_reprepare_with_other_shape_is_invalid(pool):
+    spec = spec_small("f32", key="rt_shape")
+    f = prepare(pool, spec)
+    other = spec_small("f32", key="rt_shape")
+    other.rows = [r + 1 for r in other.rows]
+    with pytest.raises(sage.SageError) as e:
+        prepare(pool, other)
+    assert e.value.status == -1
+    f.release()
+
+
+def test_budget_exhaustion_is_nomem():
+    p = sage.Pool(device=0, budget_bytes=4 << 20)
+    try:
+        spec = spec_small("f32", key="rt_nomem")
+        spec.rows = [200_000] * 4
+        with pytest.raises(sage.SageError) as e:
+            prepare(p, spec)
+        assert e.value.status == -2
+        assert p.stats()["functions"] == 0
+    finally:
+        p.destroy()
+
+
+def test_staging_failure_is_sticky_and_releases_cleanly(pool):
+    spec = spec_small("f32", key="rt_fail")
+    f = prepare(pool, spec, fail_at_call=3)
+    with pytest.raises(sage.SageError) as e:
+        f.wait()
+    assert e.value.status == -6
+    d = DevInvocation(workload.make_invocation(spec, 4, seed=1))
+    with pytest.raises(sage.SageError) as e:
+        f.invoke(*d.args())
+    assert e.value.status == -6
+    n0 = pool.stats()["functions"]
+    f.release()
+    assert pool.stats()["functions"] == n0 - 1
+
+
+def test_pool_destroy_is_busy_with_live_references():
+    p = sage.Pool(device=0)
+    spec = spec_small("f32", key="rt_busy")
+    f = prepare(p, spec)
+    with pytest.raises(sage.SageError) as e:
+        p.destroy()
+    assert e.value.status == -5
+    f.release()
+    p.destroy()
+
+
+def test_invoke_waits_for_slow_staging(pool):
+    """The pointer is handed out before the data is ready; the launch waits for it."""
+    spec = spec_small("bf16", key="rt_slow")
+    ctx, keep = workload.tables_ctx(spec)
+    real = workload.lib().wl_fill_tables
+
+    @workload.FILL_FN
+    def slow_fill(dst, off, n, c):
+        time.sleep(0.05)
+        return real(dst, off, n, ctypes.addressof(ctx))
+
+    args = workload.prepare_kwargs(spec)
+    args["tables_fill"] = ctypes.cast(slow_fill, ctypes.c_void_p).value
+    args["tables_ctx"] = None
+    args["keep"] = (args["keep"], slow_fill, ctx, keep)
+    t0 = time.time()
+    f = pool.prepare(**args)
+    assert time.time() - t0 < 0.5            # prepare does not wait for the data
+    assert f.query() == sage.SAGE_PENDING
+    d = DevInvocation(workload.make_invocation(spec, 40, seed=3))
+    f.invoke(*d.args())
+    _check_inv(spec, workload.weights_arrays(spec), d, RTOL["bf16"])
+    assert f.query() == sage.SAGE_OK
+    f.release()
+
+
+def test_out_of_range_index_reported_by_check(pool):
+    spec = spec_small("f32", key="rt_oob")
+    f = prepare(pool, spec)
+    inv = workload.make_invocation(spec, 8, seed=4)
+    inv["indices"] = inv["indices"].copy()
+    inv["indices"][0] = spec.rows[0] + 5
+    d = DevInvocation(inv)
+    f.invoke(*d.args())
+    with pytest.raises(sage.SageError) as e:
+        f.check_errors()
+    assert e.value.status == -7
+    f.check_errors()   # cleared
+    f.release()
+
+
+def test_concurrent_invocations_on_two_streams_and_threads(pool):
+    torch = _torch()
+    spec = spec_small("bf16", key="rt_conc")
+    f = prepare(pool, spec, workspace_slots=3)
+    try:
+        invs = [workload.make_invocation(spec, 64 + 10 * i, seed=300 + i) for i in range(8)]
+        ref = [DevInvocation(v) for v in invs]
+        for d in ref:
+            f.invoke(*d.args())
+        torch.cuda.synchronize()
+        got = [DevInvocation(v) for v in invs]
+        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+
+        def work(k):
+            for j in range(k, 8, 2):
+                f.invoke(*got[j].args(), stream=streams[k])
+
+        th = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+        for a, b in zip(ref, got):
+            assert torch.equal(a.out, b.out)
+    finally:
+        f.release()
+
+
+def test_workspace_grows_for_large_batches(pool):
+    spec = spec_small("f32", key="rt_grow")
+    f = prepare(pool, spec, max_batch=16)
+    try:
+        d = DevInvocation(workload.make_invocation(spec, 700, seed=5))
+        f.invoke(*d.args())
+        _check_inv(spec, workload.weights_arrays(spec), d, RTOL["f32"])
+    finally:
+        f.release()
+
+
+@pytest.mark.parametrize("serial", [False, True])
+def test_serial_and_parallel_setup_agree(serial):
+    torch = _torch()
+    p = sage.Pool(device=0, serial_setup=serial, torch_allocator=True)
+    try:
+        spec = spec_small("bf16", key="rt_setup")
+        f = prepare(p, spec, tables_in_host_memory=True)
+        d = DevInvocation(workload.make_invocation(spec, 33, seed=6))
+        f.invoke(*d.args())
+        _check_inv(spec, workload.weights_arrays(spec), d, RTOL["bf16"])
+        st = p.stats()
+        assert st["last_prepare_ms"] > 0 and st["ctx_ms"] > 0
+        f.release()
+    finally:
+        p.destroy()

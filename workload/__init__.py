@@ -392,3 +392,27 @@ def poisson_arrivals(count: int, rate_per_s: float, seed: int) -> np.ndarray:
     """Arrival times (s) of a Poisson process: cumulative exponential gaps."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+
+
+# ---------------------------------------------------------------- C-ABI arguments
+
+def prepare_kwargs(spec: FunctionSpec, fail_at_call: int = 0, tables_in_host_memory: bool = False):
+    """Keyword arguments of paper_2404_14691_b300.Pool.prepare for this function's
+    read-only data: the tables come from the C producer wl_fill_tables (or from a
+    host image when tables_in_host_memory), the weights from a host image."""
+    wblob = weights_blob(spec)
+    kw = dict(key=spec.key, dtype=spec.dtype_code, rows=list(spec.rows), dim=spec.dim, n_dense=spec.n_dense,
+              bot_dims=list(spec.bot_dims), top_dims=list(spec.top_dims), tables_bytes=spec.table_bytes(),
+              weights_bytes=int(wblob.nbytes), weights_src=wblob.ctypes.data)
+    keep = [wblob]
+    if tables_in_host_memory:
+        tb = tables_blob(spec)
+        kw["tables_src"] = tb.ctypes.data
+        keep.append(tb)
+    else:
+        ctx, k2 = tables_ctx(spec, fail_at_call=fail_at_call)
+        kw["tables_fill"] = fill_tables_fnptr()
+        kw["tables_ctx"] = ctx
+        keep.append(k2)
+    kw["keep"] = keep
+    return kw
