@@ -120,7 +120,7 @@ typedef struct {
  *   bytes = the end of the last bias rounded up to 256.
  *   Bottom layer 0 has in = n_dense; top layer 0 has in = num_tables*dim +
  *   bot_dims[n_bot-1]; the last top layer has out = 1.
- * Limits: 1 <= num_tables <= 128; dim*elem a multiple of 16 bytes and <= 1024;
+ * Limits: 1 <= num_tables <= 128; dim*elem a power of two in [16, 1024] bytes;
  *   1 <= n_dense <= 64; n_bot, n_top in [1, 8]; for SAGE_BF16 every layer but
  *   bottom 0 and the last top layer needs in and out multiples of 64 (tensor-core
  *   tiles); rows[t] < 2^31. */
@@ -149,6 +149,8 @@ typedef struct {
     const int64_t* offsets;        /* device [num_tables*B + 1], table-major CSR: bag (t,b) is
                                       indices[offsets[t*B+b] .. offsets[t*B+b+1]) */
     float* out;                    /* device [B]: sigmoid outputs */
+    int64_t num_indices;           /* optional: offsets[T*B] - offsets[0] when known on the host, else 0;
+                                      used only for the byte count of the kernel-timing record */
 } sage_invocation;
 
 /* The same invocation with HOST buffers (Writable data loaded to the GPU and the
@@ -193,6 +195,12 @@ sage_status sage_pool_create(const sage_pool_config* config, sage_pool* out);
  * Returns without waiting for the data.  A resident key re-prepared with another
  * dtype, shape or byte size returns SAGE_ERR_INVALID. */
 sage_status sage_prepare(sage_pool pool, const sage_fn_desc* desc, sage_fn* out);
+
+/* Device addresses of the function's read-only items (data_dptr of Sec. 4.1 /
+ * SageLoadToGPU of Sec. 4.2): valid while the handle lives; the bytes are there
+ * only once sage_fn_query / sage_fn_wait return SAGE_OK (kernels launched by
+ * sage_invoke* wait for them on the device).  Either output may be NULL. */
+sage_status sage_fn_data(sage_fn fn, const void** tables, const void** weights);
 
 /* Non-blocking readiness query: SAGE_OK when the read-only data is on the device,
  * SAGE_PENDING while staging, SAGE_ERR_STAGING after a producer failure. */
@@ -239,6 +247,22 @@ const char* sage_last_error(void);
 
 /* Number of kernels the library has launched in this process (all pools). */
 int64_t sage_kernel_launches(void);
+
+/* Kernel timing.  While enabled, every kernel that sage_invoke* launches is
+ * bracketed by two timing CUDA events recorded on the stream it is launched on.
+ * sage_profile_read synchronises those events, aggregates them per kernel kind
+ * (names: "bottom0", "gemm_f32", "gemm_tc", "gather", "head") into out[0..max)
+ * and clears the record; it returns the number of kinds written (or a negative
+ * sage_status).  Enabling adds two event records per kernel to the stream. */
+typedef struct {
+    char name[16];
+    int64_t launches;
+    double total_ms;
+    double work;                   /* algorithmic bytes (gather) or flops (GEMMs) summed over launches */
+} sage_kernel_time;
+
+sage_status sage_profile_enable(int on);
+int sage_profile_read(sage_kernel_time* out, int max);
 
 /* ---- building blocks (the kernels of sage_invoke, callable one by one) ----
  * Used by the parity tests and the kernel benchmarks.  All pointers are device

@@ -14,11 +14,11 @@ import ctypes
 from typing import Optional, Sequence
 
 from ._native import (DEV_ALLOC_FN, DEV_FREE_FN, SAGE_BF16, SAGE_F32, SAGE_OK, SAGE_PENDING, SAGE_READONLY,
-                      STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, PoolConfig, PoolStats, SageError,
-                      check, lib)
+                      STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, KernelTime, PoolConfig, PoolStats,
+                      SageError, check, lib)
 
 __all__ = ["Pool", "Function", "SageError", "SAGE_F32", "SAGE_BF16", "embedding_bag_sum", "linear",
-           "kernel_launches", "torch_allocator_hooks"]
+           "kernel_launches", "profile_enable", "profile_read", "torch_allocator_hooks"]
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -32,6 +32,19 @@ def _stream_handle(stream) -> Optional[int]:
 def kernel_launches() -> int:
     """Kernels launched by libsage.so in this process."""
     return int(lib().sage_kernel_launches())
+
+
+def profile_enable(on: bool) -> None:
+    """Bracket every kernel of sage_invoke* with timing events on its stream."""
+    check(lib().sage_profile_enable(1 if on else 0), "sage_profile_enable")
+
+
+def profile_read() -> dict:
+    """{kind: (launches, total_ms, work)} of the kernels timed since the last read."""
+    buf = (KernelTime * 8)()
+    n = check(lib().sage_profile_read(buf, 8), "sage_profile_read")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms), float(buf[i].work))
+            for i in range(n)}
 
 
 def torch_allocator_hooks(device: int = 0):
@@ -59,19 +72,28 @@ class Function:
         self.handle = ctypes.c_void_p(handle)
         self._keep = keep
 
+    def data(self):
+        """(tables, weights) device addresses of the read-only items."""
+        t, w = ctypes.c_void_p(), ctypes.c_void_p()
+        check(lib().sage_fn_data(self.handle, ctypes.byref(t), ctypes.byref(w)), "sage_fn_data")
+        return t.value, w.value
+
     def query(self) -> int:
         return check(lib().sage_fn_query(self.handle), "sage_fn_query")
 
     def wait(self, timeout_us: int = -1) -> None:
         check(lib().sage_fn_wait(self.handle, int(timeout_us)), "sage_fn_wait")
 
-    def invoke(self, batch: int, dense: int, indices: int, offsets: int, out: int, stream=None) -> None:
-        inv = Invocation(int(batch), dense, indices, offsets, out)
+    def invoke(self, batch: int, dense: int, indices: int, offsets: int, out: int, stream=None,
+               num_indices: int = 0) -> None:
+        inv = Invocation(int(batch), dense, indices, offsets, out, int(num_indices))
         check(lib().sage_invoke(self.handle, ctypes.byref(inv), _stream_handle(stream)), "sage_invoke")
 
     def invoke_batch(self, invs: Sequence[tuple], stream=None) -> None:
-        """invs: (batch, dense_ptr, indices_ptr, offsets_ptr, out_ptr) per invocation (device pointers)."""
-        arr = (Invocation * len(invs))(*[Invocation(int(b), d, i, o, u) for (b, d, i, o, u) in invs])
+        """invs: (batch, dense_ptr, indices_ptr, offsets_ptr, out_ptr[, num_indices]) per invocation
+        (device pointers)."""
+        arr = (Invocation * len(invs))(*[Invocation(int(v[0]), v[1], v[2], v[3], v[4], int(v[5]) if len(v) > 5 else 0)
+                                         for v in invs])
         check(lib().sage_invoke_batch(self.handle, arr, len(invs), _stream_handle(stream)), "sage_invoke_batch")
 
     def invoke_batch_host(self, invs: Sequence[tuple], stream=None) -> None:

@@ -47,7 +47,12 @@ class FnDesc(ctypes.Structure):
 
 class Invocation(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int), ("dense", ctypes.c_void_p), ("indices", ctypes.c_void_p),
-                ("offsets", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("offsets", ctypes.c_void_p), ("out", ctypes.c_void_p), ("num_indices", ctypes.c_int64)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 16), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("work", ctypes.c_double)]
 
 
 class HostInvocation(ctypes.Structure):
@@ -70,6 +75,7 @@ _vp, _i, _i64, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_siz
 SIGNATURES = [
     ("sage_pool_create", _i, [ctypes.POINTER(PoolConfig), ctypes.POINTER(_vp)]),
     ("sage_prepare", _i, [_vp, ctypes.POINTER(FnDesc), ctypes.POINTER(_vp)]),
+    ("sage_fn_data", _i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     ("sage_fn_query", _i, [_vp]),
     ("sage_fn_wait", _i, [_vp, _i64]),
     ("sage_invoke", _i, [_vp, ctypes.POINTER(Invocation), _vp]),
@@ -81,6 +87,8 @@ SIGNATURES = [
     ("sage_pool_stats_get", _i, [_vp, ctypes.POINTER(PoolStats)]),
     ("sage_last_error", ctypes.c_char_p, []),
     ("sage_kernel_launches", _i64, []),
+    ("sage_profile_enable", _i, [_i]),
+    ("sage_profile_read", _i, [ctypes.POINTER(KernelTime), _i]),
     ("sage_embedding_bag_sum", _i, [_i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     ("sage_linear", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp]),
 ]

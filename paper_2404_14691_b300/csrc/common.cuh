@@ -25,6 +25,7 @@ struct InvDesc {
   float* out;              // [batch]
   int batch;
   int row_base;
+  int64_t nidx;            // indices of the invocation if known on the host (cost model only), else 0
 };
 
 struct InvTable {

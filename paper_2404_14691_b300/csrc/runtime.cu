@@ -334,6 +334,48 @@ void stager_loop(sage_pool_s* P) {
   }
 }
 
+// ---------------------------------------------------------------- kernel timing
+
+enum ProfKind { kProfBottom0 = 0, kProfGemmF32, kProfGemmTc, kProfGather, kProfHead, kProfKinds };
+const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32", "gemm_tc", "gather", "head"};
+
+struct ProfRec {
+  int kind;
+  double work;
+  cudaEvent_t a, b;
+};
+
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+
+// Brackets one launch with timing events on its stream while profiling is on.
+struct ProfScope {
+  cudaStream_t s;
+  int kind;
+  double work;
+  cudaEvent_t a = nullptr;
+  ProfScope(cudaStream_t s_, int kind_, double work_) : s(s_), kind(kind_), work(work_) {
+    if (!g_prof_on.load(std::memory_order_relaxed)) return;
+    if (cudaEventCreate(&a) != cudaSuccess) {
+      a = nullptr;
+      return;
+    }
+    cudaEventRecord(a, s);
+  }
+  ~ProfScope() {
+    if (!a) return;
+    cudaEvent_t b;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    g_prof.push_back({kind, work, a, b});
+  }
+};
+
 // ---------------------------------------------------------------- kernels / workspace
 
 std::once_flag g_load_once;
@@ -507,6 +549,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     const Layer& L0 = e->layers[0];
     void* y = nb == 1 ? bot_out : s.bot[0];
     const int ldy = nb == 1 ? cd : e->bot[0];
+    ProfScope ps(stream, kProfBottom0, 2.0 * M * L0.in * L0.out);
     SAGE_CK(launch_bottom0(e->dtype, tab, L0.in, L0.out, L0.W, L0.b, y, ldy, stream));
   }
   for (int l = 1; l < nb; ++l) {
@@ -514,6 +557,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     const void* x = s.bot[l - 1];
     void* y = l == nb - 1 ? bot_out : s.bot[l];
     const int ldy = l == nb - 1 ? cd : e->bot[l];
+    ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : kProfGemmF32, 2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
       SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, L.in, L.W, L.b, 1, y, ldy, e->d_err, stream));
     else
@@ -534,6 +578,12 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     a.out = s.concat;
     a.ldo = cd;
     a.err = e->d_err;
+    // algorithmic bytes: each lookup reads a row and its index, each bag reads its
+    // offset and writes one pooled row
+    double lookups = 0;
+    for (int i = 0; i < tab.n; ++i) lookups += static_cast<double>(tab.d[i].nidx);
+    const double row = static_cast<double>(e->dim) * es;
+    ProfScope ps(stream, kProfGather, lookups * (row + 4.0) + static_cast<double>(e->T) * M * (8.0 + row));
     SAGE_CK(launch_gather(a, tab, stream));
   }
   // top MLP hidden layers
@@ -542,6 +592,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   for (int l = 0; l + 1 < nt; ++l) {
     const Layer& L = e->layers[nb + l];
     char* y = s.top[l];
+    ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : kProfGemmF32, 2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
       SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, ldx, L.W, L.b, 1, y, L.out, e->d_err, stream));
     else
@@ -553,6 +604,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   }
   // sigmoid head, written to each invocation's out
   const Layer& H = e->layers[nb + nt - 1];
+  ProfScope ps(stream, kProfHead, 2.0 * M * H.in);
   SAGE_CK(launch_head(e->dtype, tab, H.in, x, ldx, H.W, H.b, stream));
   return SAGE_OK;
 }
@@ -606,6 +658,42 @@ extern "C" {
 const char* sage_last_error(void) { return t_err.c_str(); }
 
 int64_t sage_kernel_launches(void) { return sage::launches(); }
+
+sage_status sage_profile_enable(int on) {
+  g_prof_on.store(on != 0);
+  return SAGE_OK;
+}
+
+int sage_profile_read(sage_kernel_time* out, int max) {
+  if (!out || max < 0) return fail(SAGE_ERR_INVALID, "bad output");
+  std::vector<ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    recs.swap(g_prof);
+  }
+  sage_kernel_time agg[kProfKinds];
+  memset(agg, 0, sizeof(agg));
+  sage_status st = SAGE_OK;
+  for (auto& r : recs) {
+    float ms = 0;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess)
+      st = fail(SAGE_ERR_CUDA, "profile events");
+    agg[r.kind].launches++;
+    agg[r.kind].total_ms += ms;
+    agg[r.kind].work += r.work;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (st != SAGE_OK) return st;
+  int n = 0;
+  for (int k = 0; k < kProfKinds && n < max; ++k) {
+    if (!agg[k].launches) continue;
+    out[n] = agg[k];
+    snprintf(out[n].name, sizeof(out[n].name), "%s", kProfNames[k]);
+    ++n;
+  }
+  return n;
+}
 
 sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
   if (!out) return fail(SAGE_ERR_INVALID, "null out");
@@ -818,6 +906,13 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
   return SAGE_OK;
 }
 
+sage_status sage_fn_data(sage_fn f, const void** tables, const void** weights) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  if (tables) *tables = f->e->d_tables;
+  if (weights) *weights = f->e->d_weights;
+  return SAGE_OK;
+}
+
 sage_status sage_fn_query(sage_fn f) {
   if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
   Entry* e = f->e;
@@ -876,6 +971,7 @@ sage_status sage_invoke_batch(sage_fn f, const sage_invocation* invs, int n, voi
         dd.out = v.out;
         dd.batch = v.batch;
         dd.row_base = static_cast<int>(M);
+        dd.nidx = v.num_indices;
         M += v.batch;
       }
       ++i;
@@ -977,6 +1073,7 @@ sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, 
       dd.out = reinterpret_cast<float*>(pu + ou);
       dd.batch = v.batch;
       dd.row_base = static_cast<int>(row);
+      dd.nidx = v.num_indices;
       dense_r.push_back({pd + od, reinterpret_cast<const char*>(v.dense), bd});
       idx_r.push_back({pi + oi, reinterpret_cast<const char*>(v.indices), bi});
       off_r.push_back({po + oo, reinterpret_cast<const char*>(v.offsets), bo});
@@ -1118,7 +1215,7 @@ sage_status sage_embedding_bag_sum(sage_dtype dtype, const void* tables, const i
   std::unique_ptr<InvTable> tab(new InvTable());
   tab->n = 1;
   tab->M = batch;
-  tab->d[0] = InvDesc{nullptr, indices, offsets, nullptr, batch, 0};
+  tab->d[0] = InvDesc{nullptr, indices, offsets, nullptr, batch, 0, 0};
   GatherArgs a;
   a.dtype = dtype;
   a.tables = static_cast<const char*>(tables);

@@ -14,6 +14,7 @@ def torch_mod():
 
 def dev(a: np.ndarray):
     torch = torch_mod()
+    assert a.dtype != np.float64, "device buffers of this library are never fp64"
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 

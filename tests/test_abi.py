@@ -13,7 +13,7 @@ HEADER = os.path.join(ROOT, "include", "sage.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:sage_status|const char\*|int64_t)\s+(sage_\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:sage_status|const char\*|int64_t|int)\s+(sage_\w+)\s*\(", src, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -59,9 +59,9 @@ def test_ctypes_struct_sizes_match_the_header():
 #include <stddef.h>
 #include "sage.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(sage_pool_config), sizeof(sage_data_desc), sizeof(sage_fn_desc),
-         sizeof(sage_invocation), sizeof(sage_host_invocation), sizeof(sage_pool_stats),
-         offsetof(sage_fn_desc, weights));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(sage_pool_config), sizeof(sage_data_desc),
+         sizeof(sage_fn_desc), sizeof(sage_invocation), sizeof(sage_host_invocation), sizeof(sage_pool_stats),
+         offsetof(sage_fn_desc, weights), sizeof(sage_kernel_time));
   return 0;
 }
 '''
@@ -72,7 +72,7 @@ int main(void) {
     got = [int(x) for x in subprocess.check_output([tmp]).split()]
     want = [ctypes.sizeof(N.PoolConfig), ctypes.sizeof(N.DataDesc), ctypes.sizeof(N.FnDesc),
             ctypes.sizeof(N.Invocation), ctypes.sizeof(N.HostInvocation), ctypes.sizeof(N.PoolStats),
-            N.FnDesc.weights.offset]
+            N.FnDesc.weights.offset, ctypes.sizeof(N.KernelTime)]
     assert got == want
     os.remove(tmp)
     os.remove(tmp + ".c")

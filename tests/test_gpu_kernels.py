@@ -144,7 +144,7 @@ def _bf16_case(M, N, K, seed):
     rnd = lambda a: torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).float().numpy()
     x = rnd(np.abs(rng.standard_normal((M, K))) * 0.5)
     W = rnd(rng.uniform(-1, 1, (N, K)) * np.sqrt(6.0 / (K + N)))
-    b = rng.uniform(-1, 1, N).astype(np.float32) / np.sqrt(K)
+    b = (rng.uniform(-1, 1, N) / np.sqrt(K)).astype(np.float32)
     return x, W, b
 
 
