@@ -264,6 +264,29 @@ typedef struct {
 sage_status sage_profile_enable(int on);
 int sage_profile_read(sage_kernel_time* out, int max);
 
+/* ---- invocation without any device allocation ----
+ * The paper has no counterpart of this entry point.  It serves callers that may
+ * not allocate device memory at all -- a latency-critical host thread that must
+ * never enter the device allocator, or a runtime that owns every device byte
+ * itself -- and so cannot hold a sage_fn, whose workspace the pool allocates.
+ * It runs one invocation exactly like sage_invoke (same kernels, same results
+ * within the same tolerances), but takes the function's shape (`shape`; its two
+ * data items are ignored) and its read-only data as caller-owned device
+ * pointers: `tables` and `weights` laid out as the tables / weights items of
+ * sage_fn_desc.  The caller passes inputs and outputs in `inv` as for sage_invoke.
+ * Its activations and error word live in one static device array of 64 MiB that
+ * every GPU loading this library holds until exit; a batch whose activations do
+ * not fit is rejected with SAGE_ERR_INVALID and a message giving the bytes
+ * needed.  It calls no allocator (no cudaMalloc/cudaMallocAsync/cudaFree, no
+ * library routine that allocates).  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents: calls whose kernels overlap on the GPU race,
+ * so issue them on one stream (or order them).  Out-of-range bag rows are
+ * skipped; the error word is not reported.  Asynchronous on `stream`. */
+sage_status sage_invoke_noalloc(const sage_fn_desc* shape, const void* tables, const void* weights,
+                                const sage_invocation* inv, void* stream);
+
 /* ---- building blocks (the kernels of sage_invoke, callable one by one) ----
  * Used by the parity tests and the kernel benchmarks.  All pointers are device
  * pointers; all calls are asynchronous on `stream`; err_word (device int, may be

@@ -89,6 +89,7 @@ SIGNATURES = [
     ("sage_kernel_launches", _i64, []),
     ("sage_profile_enable", _i, [_i]),
     ("sage_profile_read", _i, [ctypes.POINTER(KernelTime), _i]),
+    ("sage_invoke_noalloc", _i, [ctypes.POINTER(FnDesc), _vp, _vp, ctypes.POINTER(Invocation), _vp]),
     ("sage_embedding_bag_sum", _i, [_i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     ("sage_linear", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp]),
 ]

@@ -7,6 +7,9 @@
 
 namespace sage {
 
+// Sets the thread-local message that sage_last_error() returns.
+void set_last_error(const char* msg);
+
 // Kernels launched by this library so far (all pools, all threads).
 void count_launch(int n = 1);
 int64_t launches();

@@ -47,6 +47,12 @@ sage_status fail(sage_status st, const char* fmt, ...) {
   return st;
 }
 
+}  // namespace
+
+void sage::set_last_error(const char* msg) { t_err = msg; }
+
+namespace {
+
 #define SAGE_CK(call)                                                                                  \
   do {                                                                                                 \
     cudaError_t e_ = (call);                                                                           \
