@@ -51,16 +51,17 @@ def make_workload(name: str, rank: int = 0):
         invs = [workload.make_invocation(spec, 256, seed=workload.sub_seed("c1", "inv", rank) % (1 << 63))]
         desc = "plain-fp32: 1 invocation, B=256, L=20, Zipf(1.05); tables 8x100000x64 fp32"
         return spec, invs, desc
-    if name in ("c3", "c3-uniform"):
-        spec = workload.spec_c3()
+    if name in ("c3", "c3-uniform", "c3s", "c3s-uniform"):
+        small = name.startswith("c3s")
+        spec = workload.spec_c3("c3s_bf16_26x200k_d128", rows=200_000) if small else workload.spec_c3()
         sizes = workload.batch_sizes_lognormal(128, seed=workload.sub_seed("c3", "sizes", rank))
-        uni = name == "c3-uniform"
+        uni = name.endswith("-uniform")
         invs = [workload.make_invocation(spec, int(B), seed=workload.sub_seed("c3", "inv", rank, i) % (1 << 63),
                                          uniform_rows=uni)
                 for i, B in enumerate(sizes)]
         desc = ("precision-bf16: 128 invocations, B~round(LogNormal(ln256,1)) in [1,4096], L~U[1,100], %s; "
-                "tables 26x1000000x128 bf16; MLP 13-512-256-128 / 3456-1024-512-256-1"
-                % ("uniform rows (no reuse)" if uni else "Zipf(1.1)"))
+                "tables 26x%dx128 bf16; MLP 13-512-256-128 / 3456-1024-512-256-1"
+                % ("uniform rows (no reuse)" if uni else "Zipf(1.1)", spec.rows[0]))
         return spec, invs, desc
     raise SystemExit("unknown workload %s" % name)
 
