@@ -264,6 +264,57 @@ typedef struct {
 sage_status sage_profile_enable(int on);
 int sage_profile_read(sage_kernel_time* out, int max);
 
+/* ---- serving ----
+ * sage_serve replays a trace of timed requests against several functions on the
+ * pool's GPU with continuous batching (the project's serving form; the paper's
+ * evaluation replays a trace of function requests, Sec. 7.1).  Each function is
+ * prepared when its first request arrives (cold setup: staging beside kernel
+ * loading, Sec. 4.1) and its requests queue until its data is ready.  Admission
+ * is by device memory: a prepare that exceeds the pool budget evicts idle
+ * resident functions (least recently used first) or waits.  Every function owns
+ * lanes_per_fn streams, each with its own workspace slot; an idle lane takes ALL
+ * queued requests of its function (up to the batch limits) as one fused batch,
+ * so requests arriving while others run join the next batch, and lanes of
+ * different functions overlap on the device.  An idle function keeps its data
+ * for linger_s (stage 1 of the multi-stage exit, Sec. 5.3), then is released.
+ * Request buffers are host memory (pinned recommended): inputs are copied in and
+ * outputs copied back inside each batch.  Latency = completion - arrival. */
+typedef struct {
+    int fn;                        /* index into fns[] */
+    double arrival_s;              /* arrival time, seconds from the start of the replay */
+    sage_host_invocation inv;      /* the request's host buffers */
+} sage_request;
+
+typedef struct {
+    int max_batch_invocations;     /* requests per fused batch, <= 256; 0 = 256 */
+    int64_t max_batch_rows;        /* samples per fused batch; 0 = 65536 (a single larger request still runs) */
+    int lanes_per_fn;              /* concurrent batches per function; 0 = 2 */
+    double linger_s;               /* keep an idle function resident this long; < 0 = until evicted */
+    double timeout_s;              /* give up after this long (SAGE_ERR_TIMEOUT); 0 = 600 */
+} sage_serve_config;
+
+typedef struct {
+    double latency_ms;             /* completion - arrival (-1 if it did not complete) */
+    double queue_ms;               /* launch - arrival: queueing incl. waiting for a cold setup */
+    double service_ms;             /* completion - launch */
+    int cold;                      /* 1: its function was not resident and ready when it arrived */
+    int batch_invocations;         /* requests fused into its batch */
+    int status;                    /* sage_status of this request */
+} sage_request_result;
+
+typedef struct {
+    double wall_s;
+    int64_t completed, batches, prepares, evictions, cold_requests, max_inflight_batches;
+    double invocations_per_s;      /* completed / wall_s */
+    double mean_ms, p50_ms, p99_ms, warm_p50_ms, warm_p99_ms, cold_p50_ms, cold_p99_ms;
+} sage_serve_stats;
+
+/* fns[]: the functions (their data items must stay valid for the whole replay);
+ * reqs[]: n requests (any order); results[]: n outputs (required); stats may be
+ * NULL.  Returns SAGE_OK when every request completed, else the first error. */
+sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n_fns, const sage_request* reqs, int n,
+                       const sage_serve_config* config, sage_request_result* results, sage_serve_stats* stats);
+
 /* ---- invocation without any device allocation ----
  * The paper has no counterpart of this entry point.  It serves callers that may
  * not allocate device memory at all -- a latency-critical host thread that must

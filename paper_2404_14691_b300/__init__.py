@@ -15,10 +15,10 @@ from typing import Optional, Sequence
 
 from ._native import (DEV_ALLOC_FN, DEV_FREE_FN, SAGE_BF16, SAGE_F32, SAGE_OK, SAGE_PENDING, SAGE_READONLY,
                       STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, KernelTime, PoolConfig, PoolStats,
-                      SageError, check, lib)
+                      Request, RequestResult, SageError, ServeConfig, ServeStats, check, lib)
 
 __all__ = ["Pool", "Function", "SageError", "SAGE_F32", "SAGE_BF16", "embedding_bag_sum", "linear",
-           "kernel_launches", "profile_enable", "profile_read", "torch_allocator_hooks"]
+           "kernel_launches", "profile_enable", "profile_read", "torch_allocator_hooks", "serve"]
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -62,6 +62,46 @@ def torch_allocator_hooks(device: int = 0):
         torch.cuda.caching_allocator_delete(ptr)
 
     return DEV_ALLOC_FN(_alloc), DEV_FREE_FN(_free)
+
+
+def fn_desc(key: str, dtype: int, rows: Sequence[int], dim: int, n_dense: int, bot_dims: Sequence[int],
+            top_dims: Sequence[int], tables_bytes: int, weights_bytes: int, tables_src: Optional[int] = None,
+            tables_fill: Optional[int] = None, tables_ctx=None, weights_src: Optional[int] = None,
+            max_batch: int = 0, workspace_slots: int = 0, keep=None):
+    """A sage_fn_desc and the Python objects it points into.  tables_src / weights_src:
+    host addresses of the data items; or tables_fill: address of a C producer
+    (sage_fill_fn) with tables_ctx."""
+    T = len(rows)
+    rows_a = (ctypes.c_int64 * T)(*rows)
+    bot_a = (ctypes.c_int * len(bot_dims))(*bot_dims)
+    top_a = (ctypes.c_int * len(top_dims))(*top_dims)
+    kb = key.encode()
+    ctx_ptr = ctypes.cast(ctypes.byref(tables_ctx), ctypes.c_void_p) if tables_ctx is not None else None
+    tdesc = DataDesc(kb, SAGE_READONLY, tables_bytes, tables_src, tables_fill, ctx_ptr)
+    wdesc = DataDesc(kb, SAGE_READONLY, weights_bytes, weights_src, None, None)
+    d = FnDesc(kb, dtype, T, rows_a, dim, n_dense, len(bot_dims), bot_a, len(top_dims), top_a,
+               max_batch, workspace_slots, tdesc, wdesc)
+    return d, (rows_a, bot_a, top_a, kb, tables_ctx, keep)
+
+
+def serve(pool: "Pool", functions: Sequence[dict], requests: Sequence[tuple], max_batch_invocations: int = 0,
+          max_batch_rows: int = 0, lanes_per_fn: int = 0, linger_s: float = -1.0, timeout_s: float = 0.0):
+    """Replay a request trace with continuous batching (sage_serve).
+
+    functions: fn_desc keyword dicts; requests: (fn, arrival_s, batch, dense, indices, offsets,
+    num_indices, out) with host addresses.  Returns (results, stats): results is a list of
+    dicts per request, stats a dict."""
+    descs = [fn_desc(**kw) for kw in functions]
+    arr = (FnDesc * len(descs))(*[d for d, _ in descs])
+    reqs = (Request * len(requests))(*[Request(int(f), float(t), HostInvocation(int(b), d, i, o, int(ni), u))
+                                       for (f, t, b, d, i, o, ni, u) in requests])
+    res = (RequestResult * max(1, len(requests)))()
+    st = ServeStats()
+    cfg = ServeConfig(max_batch_invocations, max_batch_rows, lanes_per_fn, linger_s, timeout_s)
+    check(lib().sage_serve(pool.handle, arr, len(descs), reqs, len(requests), ctypes.byref(cfg), res,
+                           ctypes.byref(st)), "sage_serve")
+    out = [{name: getattr(res[k], name) for name, _ in RequestResult._fields_} for k in range(len(requests))]
+    return out, {name: getattr(st, name) for name, _ in ServeStats._fields_}
 
 
 class Function:
@@ -129,26 +169,12 @@ class Pool:
         check(lib().sage_pool_create(ctypes.byref(cfg), ctypes.byref(h)), "sage_pool_create")
         self.handle = h
 
-    def prepare(self, key: str, dtype: int, rows: Sequence[int], dim: int, n_dense: int,
-                bot_dims: Sequence[int], top_dims: Sequence[int], tables_bytes: int, weights_bytes: int,
-                tables_src: Optional[int] = None, tables_fill: Optional[int] = None, tables_ctx=None,
-                weights_src: Optional[int] = None, max_batch: int = 0, workspace_slots: int = 0,
-                keep=None) -> Function:
-        """Prepare a function.  tables_src / weights_src: host addresses of the data
-        items; or tables_fill: address of a C producer (sage_fill_fn) with tables_ctx."""
-        T = len(rows)
-        rows_a = (ctypes.c_int64 * T)(*rows)
-        bot_a = (ctypes.c_int * len(bot_dims))(*bot_dims)
-        top_a = (ctypes.c_int * len(top_dims))(*top_dims)
-        kb = key.encode()
-        ctx_ptr = ctypes.cast(ctypes.byref(tables_ctx), ctypes.c_void_p) if tables_ctx is not None else None
-        tdesc = DataDesc(kb, SAGE_READONLY, tables_bytes, tables_src, tables_fill, ctx_ptr)
-        wdesc = DataDesc(kb, SAGE_READONLY, weights_bytes, weights_src, None, None)
-        d = FnDesc(kb, dtype, T, rows_a, dim, n_dense, len(bot_dims), bot_a, len(top_dims), top_a,
-                   max_batch, workspace_slots, tdesc, wdesc)
+    def prepare(self, **kw) -> Function:
+        """Prepare a function (keyword arguments of fn_desc)."""
+        d, keep = fn_desc(**kw)
         h = ctypes.c_void_p()
         check(lib().sage_prepare(self.handle, ctypes.byref(d), ctypes.byref(h)), "sage_prepare")
-        return Function(self, h.value, (rows_a, bot_a, top_a, kb, tables_ctx, keep))
+        return Function(self, h.value, keep)
 
     def stats(self) -> dict:
         s = PoolStats()

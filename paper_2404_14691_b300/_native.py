@@ -60,6 +60,29 @@ class HostInvocation(ctypes.Structure):
                 ("offsets", ctypes.c_void_p), ("num_indices", ctypes.c_int64), ("out", ctypes.c_void_p)]
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("fn", ctypes.c_int), ("arrival_s", ctypes.c_double), ("inv", HostInvocation)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_batch_invocations", ctypes.c_int), ("max_batch_rows", ctypes.c_int64),
+                ("lanes_per_fn", ctypes.c_int), ("linger_s", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("latency_ms", ctypes.c_double), ("queue_ms", ctypes.c_double), ("service_ms", ctypes.c_double),
+                ("cold", ctypes.c_int), ("batch_invocations", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("wall_s", ctypes.c_double), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("prepares", ctypes.c_int64), ("evictions", ctypes.c_int64), ("cold_requests", ctypes.c_int64),
+                ("max_inflight_batches", ctypes.c_int64), ("invocations_per_s", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("warm_p50_ms", ctypes.c_double), ("warm_p99_ms", ctypes.c_double),
+                ("cold_p50_ms", ctypes.c_double), ("cold_p99_ms", ctypes.c_double)]
+
+
 class PoolStats(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_size_t), ("resident_bytes", ctypes.c_size_t),
                 ("readonly_bytes", ctypes.c_size_t), ("functions", ctypes.c_int64), ("refs", ctypes.c_int64),
@@ -89,6 +112,8 @@ SIGNATURES = [
     ("sage_kernel_launches", _i64, []),
     ("sage_profile_enable", _i, [_i]),
     ("sage_profile_read", _i, [ctypes.POINTER(KernelTime), _i]),
+    ("sage_serve", _i, [_vp, ctypes.POINTER(FnDesc), _i, ctypes.POINTER(Request), _i, ctypes.POINTER(ServeConfig),
+                        ctypes.POINTER(RequestResult), ctypes.POINTER(ServeStats)]),
     ("sage_invoke_noalloc", _i, [ctypes.POINTER(FnDesc), _vp, _vp, ctypes.POINTER(Invocation), _vp]),
     ("sage_embedding_bag_sum", _i, [_i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     ("sage_linear", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp]),

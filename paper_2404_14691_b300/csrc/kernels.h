@@ -4,11 +4,15 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "../../include/sage.h"
 
 namespace sage {
 
 // Sets the thread-local message that sage_last_error() returns.
 void set_last_error(const char* msg);
+
+// Asynchronous fused batch from host buffers on a chosen workspace slot (-1: next in turn).
+sage_status host_batch_async(sage_fn f, const sage_host_invocation* invs, int n, cudaStream_t s, int slot);
 
 // Kernels launched by this library so far (all pools, all threads).
 void count_launch(int n = 1);

@@ -616,9 +616,10 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
 }
 
 // Pick a slot able to hold M rows; called with e->imu held.
-sage_status acquire_slot(Entry* e, int M, cudaStream_t stream, Slot** out) {
-  Slot& s = e->slots[e->next_slot];
-  e->next_slot = (e->next_slot + 1) % static_cast<int>(e->slots.size());
+sage_status acquire_slot(Entry* e, int M, cudaStream_t stream, Slot** out, int which = -1) {
+  if (which >= static_cast<int>(e->slots.size())) return fail(SAGE_ERR_INVALID, "slot %d out of range", which);
+  Slot& s = which >= 0 ? e->slots[which] : e->slots[e->next_slot];
+  if (which < 0) e->next_slot = (e->next_slot + 1) % static_cast<int>(e->slots.size());
   if (s.used) SAGE_CK(cudaStreamWaitEvent(stream, s.done, 0));
   if (M > s.cap) {
     // grow: wait for the slot's last use, then reallocate (rare)
@@ -996,21 +997,20 @@ sage_status sage_invoke(sage_fn f, const sage_invocation* inv, void* stream) {
   return sage_invoke_batch(f, inv, 1, stream);
 }
 
-sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, int n, void* stream) {
+}  // extern "C"
+
+// Fused batch from host buffers, asynchronous on `stream`: merged H2D copies of
+// the inputs into the slot's I/O arena, the launch chain, merged D2H copies of the
+// outputs.  slot >= 0 pins the workspace slot (the serving loop gives each of its
+// lanes its own slot); -1 takes the next slot in turn.
+sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, int n, cudaStream_t s, int slot) {
   if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
   if (n < 0 || (n > 0 && !invs)) return fail(SAGE_ERR_INVALID, "bad invocation list");
-  if (n > kMaxInv) {
-    for (int i = 0; i < n; i += kMaxInv) {
-      sage_status st = sage_invoke_batch_host(f, invs + i, std::min(kMaxInv, n - i), stream);
-      if (st != SAGE_OK) return st;
-    }
-    return SAGE_OK;
-  }
+  if (n > kMaxInv) return fail(SAGE_ERR_INVALID, "more than %d invocations in one host batch", kMaxInv);
   Entry* e = f->e;
   sage_status st = wait_ready_enqueued(e);
   if (st != SAGE_OK) return st;
   SAGE_CK(cudaSetDevice(e->pool->device));
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   // arena regions: dense | indices | offsets | out, each invocation's part 256-aligned
   size_t nd = 0, ni = 0, no = 0, nu = 0;
   int64_t M = 0;
@@ -1032,7 +1032,7 @@ sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, 
   {
     std::lock_guard<std::mutex> g(e->imu);
     Slot* sl = nullptr;
-    st = acquire_slot(e, static_cast<int>(M), s, &sl);
+    st = acquire_slot(e, static_cast<int>(M), s, &sl, slot);
     if (st != SAGE_OK) return st;
     if (sl->io_bytes < need) {
       if (sl->used) SAGE_CK(cudaEventSynchronize(sl->done));
@@ -1118,9 +1118,22 @@ sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, 
     sl->used = true;
   }
   e->pool->invocations += n;
+  return SAGE_OK;
+}
+
+extern "C" {
+
+sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, int n, void* stream) {
+  if (n < 0 || (n > 0 && !invs)) return fail(SAGE_ERR_INVALID, "bad invocation list");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; i += kMaxInv) {
+    sage_status st = sage::host_batch_async(f, invs + i, std::min(kMaxInv, n - i), s, -1);
+    if (st != SAGE_OK) return st;
+  }
   SAGE_CK(cudaStreamSynchronize(s));
   return SAGE_OK;
 }
+
 
 sage_status sage_fn_check(sage_fn f) {
   if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
