@@ -251,9 +251,11 @@ int64_t sage_kernel_launches(void);
 /* Kernel timing.  While enabled, every kernel that sage_invoke* launches is
  * bracketed by two timing CUDA events recorded on the stream it is launched on.
  * sage_profile_read synchronises those events, aggregates them per kernel kind
- * (names: "bottom0", "gemm_f32", "gemm_tc", "gather", "head") into out[0..max)
+ * (names: "bottom0", "gemm_f32", "gemm_tc", "gemm_tf32x3", "gather", "head") into out[0..max)
  * and clears the record; it returns the number of kinds written (or a negative
- * sage_status).  Enabling adds two event records per kernel to the stream. */
+ * sage_status).  Enabling adds two event records per kernel to the stream and
+ * runs the bottom MLP on the launch stream instead of beside the gather, so that
+ * every kernel's events time it alone. */
 typedef struct {
     char name[16];
     int64_t launches;
@@ -356,7 +358,9 @@ sage_status sage_embedding_bag_sum(sage_dtype dtype, const void* tables, const i
 
 /* Linear layer y = act(x W^T + bias) for M rows: x [M, K] (row stride ldx),
  * W [N, K] row-major, bias [N] fp32, y [M, N] (row stride ldy); act 0 = none,
- * 1 = ReLU.  SAGE_F32: fp32 in/out, fp32 FMA in a fixed K order.  SAGE_BF16:
+ * 1 = ReLU.  SAGE_F32: fp32 in/out; when N is a multiple of 64 (and rows are
+ * 16-byte aligned) on the tensor cores as three tf32 products of the hi/lo split
+ * of x and W (error below ~3*2^-22 * sum|x||w|), else fp32 FMA.  SAGE_BF16:
  * bf16 in/out, tcgen05 tensor cores with fp32 accumulation in tensor memory;
  * needs K and N multiples of 64 and 16-byte aligned rows. */
 sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,

@@ -1,0 +1,234 @@
+// fp32 GEMM on the 5th-generation tensor cores with a three-term tf32 split:
+//     Y[M, N] = act(X[M, K] W[N, K]^T + b)
+// x = x_hi + x_lo with x_hi = tf32(x) (round to nearest) and x_lo = x - x_hi
+// (exact in fp32), likewise for W; the product is accumulated in fp32 tensor
+// memory as x_hi w_hi + x_hi w_lo + x_lo w_hi.  The dropped x_lo w_lo term and
+// the tf32 rounding of the lo parts are each below 2^-22 of |x||w|, so every
+// output is within about 3 * 2^-22 * sum_k |x_k||w_k| of the exact dot product
+// -- fp32-level accuracy at tensor-core speed.
+//
+// One CTA computes a 128 x BN tile with 6 warps:
+//   warp 0, one lane : TMA producer, 128x32 fp32 tiles of X and BNx32 of W
+//                      (128-byte swizzle) into a STAGES-deep ring;
+//   warps 2-5        : splitters -- per stage, rewrite each loaded tile in place
+//                      as its tf32 hi part and write its lo part to a twin buffer
+//                      (same swizzled layout), then fence for the async proxy;
+//   warp 1, one lane : MMA issuer -- per 8-wide k-step three tcgen05.mma
+//                      kind::tf32 into a 128 x BN fp32 TMEM accumulator;
+//   warps 2-5        : epilogue -- tcgen05.ld of 32 TMEM lanes each, bias, ReLU,
+//                      fp32 16-byte stores.
+// Each output's k order is fixed, so a row's result does not depend on M.
+#include "kernels.h"
+
+namespace sage {
+namespace {
+
+constexpr int kBM = 128, kBK = 32;  // 32 fp32 = one 128-byte swizzle row
+constexpr int kPipeBytes = 192 * 1024;
+
+template <int BN>
+struct Tf32Cfg {
+  static constexpr int A_BYTES = kBM * kBK * 4;  // 16 KB
+  static constexpr int B_BYTES = BN * kBK * 4;
+  static constexpr int STAGE = 2 * (A_BYTES + B_BYTES);  // hi + lo of both operands
+  static constexpr int STAGES = kPipeBytes / STAGE;
+  static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
+  static_assert(STAGES >= 2, "pipeline depth");
+};
+
+constexpr int kSplitThreads = 128;  // warps 2..5
+
+// In place: v -> tf32(v); lo buffer: v - tf32(v).  `n4` float4 per thread-stride pass.
+__device__ __forceinline__ void split_tile(float* hi, float* lo, int nfloat, int tid) {
+  float4* h4 = reinterpret_cast<float4*>(hi);
+  float4* l4 = reinterpret_cast<float4*>(lo);
+  for (int q = tid; q < nfloat / 4; q += kSplitThreads) {
+    const float4 v = h4[q];
+    float4 h, l;
+    h.x = to_tf32_rna(v.x);
+    h.y = to_tf32_rna(v.y);
+    h.z = to_tf32_rna(v.z);
+    h.w = to_tf32_rna(v.w);
+    l.x = v.x - h.x;
+    l.y = v.y - h.y;
+    l.z = v.z - h.z;
+    l.w = v.w - h.w;
+    h4[q] = h;
+    l4[q] = l;
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
+                       int N, int K, const float* __restrict__ bias, int relu, float* __restrict__ Y, int ldy,
+                       int* err) {
+  using C = Tf32Cfg<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // per stage: A_hi | B_hi | A_lo | B_lo
+  auto a_hi = [&](int s) { return smem + s * C::STAGE; };
+  auto b_hi = [&](int s) { return smem + s * C::STAGE + C::A_BYTES; };
+  auto a_lo = [&](int s) { return smem + s * C::STAGE + C::A_BYTES + C::B_BYTES; };
+  auto b_lo = [&](int s) { return smem + s * C::STAGE + 2 * C::A_BYTES + C::B_BYTES; };
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* split = full + C::STAGES;
+  uint64_t* empty = split + C::STAGES;
+  uint64_t* accum = empty + C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
+  const int KB = (K + kBK - 1) / kBK;
+
+  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  if (warp == 1 && lane == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&split[s], kSplitThreads);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 2 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (kb / C::STAGES) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, err)) break;
+        mbar_arrive_expect_tx(&full[s], C::A_BYTES + C::B_BYTES);
+        tma_load_2d(a_hi(s), &tmA, kb * kBK, m0, &full[s]);
+        tma_load_2d(b_hi(s), &tmB, kb * kBK, n0, &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer: hi*hi + hi*lo + lo*hi per 8-wide k-step
+      constexpr uint32_t idesc = idesc_tf32_f32(kBM, BN);
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % C::STAGES;
+        const uint32_t ph = (kb / C::STAGES) & 1;
+        if (!mbar_wait(&split[s], ph, err)) break;
+        tc_fence_after();
+        const uint32_t ah = smem_u32(a_hi(s)), bh = smem_u32(b_hi(s));
+        const uint32_t al = smem_u32(a_lo(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+        for (int k = 0; k < kBK / 8; ++k) {
+          const uint32_t o = k * 32;  // 8 fp32 = 32 bytes along K inside the swizzle row
+          tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
+          tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+          tc_mma_tf32(tmem, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
+        }
+        tc_commit(&empty[s]);
+      }
+      tc_commit(accum);
+    }
+  } else {
+    // ---- splitters
+    const int tid = threadIdx.x - 64;
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (kb / C::STAGES) & 1;
+      if (!mbar_wait(&full[s], ph, err)) break;
+      split_tile(reinterpret_cast<float*>(a_hi(s)), reinterpret_cast<float*>(a_lo(s)), kBM * kBK, tid);
+      split_tile(reinterpret_cast<float*>(b_hi(s)), reinterpret_cast<float*>(b_lo(s)), BN * kBK, tid);
+      fence_proxy_async_smem();
+      mbar_arrive(&split[s]);
+    }
+  }
+  __syncwarp();
+
+  // ---- epilogue (warps 2-5; warp w reads TMEM lanes 32*(w%4) .. +31)
+  if (warp >= 2) {
+    mbar_wait(accum, 0, err);
+    tc_fence_after();
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    float* yrow = Y + static_cast<size_t>(row < M ? row : 0) * ldy + n0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld_32cols(tmem + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+      tmem_ld_wait();
+      if (row < M) {
+        float4* dst = reinterpret_cast<float4*>(yrow + c0);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4 o;
+          o.x = __uint_as_float(v[4 * j + 0]) + __ldg(bias + n0 + c0 + 4 * j + 0);
+          o.y = __uint_as_float(v[4 * j + 1]) + __ldg(bias + n0 + c0 + 4 * j + 1);
+          o.z = __uint_as_float(v[4 * j + 2]) + __ldg(bias + n0 + c0 + 4 * j + 2);
+          o.w = __uint_as_float(v[4 * j + 3]) + __ldg(bias + n0 + c0 + 4 * j + 3);
+          if (relu) {
+            o.x = fmaxf(o.x, 0.f);
+            o.y = fmaxf(o.y, 0.f);
+            o.z = fmaxf(o.z, 0.f);
+            o.w = fmaxf(o.w, 0.f);
+          }
+          dst[j] = o;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+template <int BN>
+cudaError_t launch_bn(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias, int relu,
+                      float* y, int ldy, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Tf32Cfg<BN>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap ta, tb;
+  if (!make_tmap_2d(&ta, 0, x, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tb, 0, W, N, K, K, kBK, BN))
+    return cudaErrorInvalidValue;
+  dim3 grid(N / BN, (M + kBM - 1) / kBM);
+  gemm_tf32x3_kernel<BN><<<grid, 192, Tf32Cfg<BN>::SMEM, s>>>(ta, tb, M, N, K, bias, relu, y, ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int g_sms = 0;
+
+}  // namespace
+
+void preload_tf32_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<128>);
+}
+
+cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
+                                 int relu, float* y, int ldy, int* err, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  if (K <= 0 || (K % 4) || (N % 64) || (ldx % 4) || (ldy % 4) || (reinterpret_cast<uintptr_t>(x) & 15) ||
+      (reinterpret_cast<uintptr_t>(W) & 15) || (reinterpret_cast<uintptr_t>(y) & 15))
+    return cudaErrorInvalidValue;
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int mt = (M + kBM - 1) / kBM;
+  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  return launch_bn<64>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+}
+
+}  // namespace sage

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include "common.cuh"
 #include "../../include/sage.h"
 
@@ -42,16 +44,26 @@ cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const v
 cudaError_t launch_head(int dtype, const InvTable& tab, int K, const void* h, int ldh, const void* w,
                         const float* c, cudaStream_t s);
 
+// 2-D TMA tensor map of a row-major matrix [rows, cols] (row stride ld elements;
+// dtype 0 fp32, 1 bf16), boxes of box_rows x box_cols, 128-byte swizzle, zero
+// fill outside the matrix.
+bool make_tmap_2d(CUtensorMap* m, int dtype, const void* base, int rows, int cols, int ld, int box_cols,
+                  int box_rows);
+
 // Dense layers y = act(x W^T + b).
 cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
                               int relu, float* y, int ldy, cudaStream_t s);
 cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, const void* W,
                                   const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s);
+// fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.
+cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
+                                 int relu, float* y, int ldy, int* err, cudaStream_t s);
 
 // Kernel loading: query every kernel of a translation unit once, which makes the
 // CUDA runtime load its module (lazy loading defers this to first use).
 void preload_gather_kernels();
 void preload_simt_kernels();
 void preload_tc_kernels();
+void preload_tf32_kernels();
 
 }  // namespace sage

@@ -201,6 +201,65 @@ __global__ void __launch_bounds__(256) bottom0_kernel(const __grid_constant__ In
   }
 }
 
+// Bottom layer 0 for thin inputs (K <= 16): a block owns 32 rows and all N
+// outputs; each thread keeps one output column's weights in registers and walks
+// the block's rows, whose dense features sit in shared memory (broadcast reads).
+// Stores are coalesced along the output row.  Same per-output order as above
+// (k = 0..K-1 FMA chain, then the bias).
+template <bool BF16>
+__global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant__ InvTable tab, int K, int N,
+                                                           const void* __restrict__ Wv,
+                                                           const float* __restrict__ bias, void* __restrict__ y,
+                                                           int ldy) {
+  constexpr int R = 32, KM = 16;
+  __shared__ float sx[R][KM];
+  __shared__ const float* srow[R];
+  const int r0 = blockIdx.x * R;
+  if (threadIdx.x < R) {
+    const int r = r0 + threadIdx.x;
+    const float* p = nullptr;
+    if (r < tab.M) {
+      const int i = tab.n == 1 ? 0 : find_inv(tab, r);
+      p = tab.d[i].dense + static_cast<size_t>(r - tab.d[i].row_base) * K;
+    }
+    srow[threadIdx.x] = p;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * KM; e += blockDim.x) {
+    const int rr = e / KM, k = e % KM;
+    sx[rr][k] = (srow[rr] && k < K) ? srow[rr][k] : 0.f;
+  }
+  __syncthreads();
+  const int nrows = min(R, tab.M - r0);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float w[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      if (k < K) {
+        if (BF16) {
+          const uint16_t u = reinterpret_cast<const uint16_t*>(Wv)[static_cast<size_t>(j) * K + k];
+          w[k] = __uint_as_float(static_cast<uint32_t>(u) << 16);
+        } else {
+          w[k] = reinterpret_cast<const float*>(Wv)[static_cast<size_t>(j) * K + k];
+        }
+      } else {
+        w[k] = 0.f;
+      }
+    }
+    const float bj = bias[j];
+    for (int rr = 0; rr < nrows; ++rr) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < KM; ++k)
+        if (k < K) s = fmaf(sx[rr][k], w[k], s);
+      s = fmaxf(s + bj, 0.f);
+      const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
+      if (BF16) reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(s);
+      else reinterpret_cast<float*>(y)[o] = s;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- head
 // One warp per batch row: z = h . w + c (lane partial sums over k = lane, lane+32,
 // ..., then a fixed xor tree), out = 1 / (1 + exp(-z)) written to the row's
@@ -250,6 +309,8 @@ void preload_simt_kernels() {
   cudaFuncGetAttributes(&fa, sgemm_nt_kernel<128, 128, 16>);
   cudaFuncGetAttributes(&fa, bottom0_kernel<false>);
   cudaFuncGetAttributes(&fa, bottom0_kernel<true>);
+  cudaFuncGetAttributes(&fa, bottom0_thin_kernel<false>);
+  cudaFuncGetAttributes(&fa, bottom0_thin_kernel<true>);
   cudaFuncGetAttributes(&fa, head_kernel<false>);
   cudaFuncGetAttributes(&fa, head_kernel<true>);
 }
@@ -275,6 +336,13 @@ cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const v
                            void* y, int ldy, cudaStream_t s) {
   if (tab.M <= 0) return cudaSuccess;
   if (K < 1 || K > 64) return cudaErrorInvalidValue;
+  if (K <= 16) {
+    const int blocks = (tab.M + 31) / 32;
+    if (dtype == 1) bottom0_thin_kernel<true><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy);
+    else bottom0_thin_kernel<false><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy);
+    count_launch();
+    return cudaGetLastError();
+  }
   const size_t smem = (static_cast<size_t>(N) * K + N) * sizeof(float);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   int blocks = (tab.M + 7) / 8;

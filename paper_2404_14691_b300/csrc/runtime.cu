@@ -158,6 +158,9 @@ struct Slot {
   size_t io_bytes = 0;
   cudaEvent_t done = nullptr;
   bool used = false;
+  // the bottom MLP runs on `branch` beside the gather (fork / join events)
+  cudaStream_t branch = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 }  // namespace
@@ -342,8 +345,8 @@ void stager_loop(sage_pool_s* P) {
 
 // ---------------------------------------------------------------- kernel timing
 
-enum ProfKind { kProfBottom0 = 0, kProfGemmF32, kProfGemmTc, kProfGather, kProfHead, kProfKinds };
-const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32", "gemm_tc", "gather", "head"};
+enum ProfKind { kProfBottom0 = 0, kProfGemmF32, kProfGemmTc, kProfGather, kProfHead, kProfGemmTf32, kProfKinds };
+const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32", "gemm_tc", "gather", "head", "gemm_tf32x3"};
 
 struct ProfRec {
   int kind;
@@ -394,6 +397,7 @@ double load_kernels_once() {
     preload_gather_kernels();
     preload_simt_kernels();
     preload_tc_kernels();
+    preload_tf32_kernels();
     g_load_ms = ms_since(t0);
     spent = g_load_ms;
   });
@@ -515,6 +519,12 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
       cudaEventSynchronize(s.done);
       cudaEventDestroy(s.done);
     }
+    if (s.branch) {
+      cudaStreamSynchronize(s.branch);
+      cudaStreamDestroy(s.branch);
+    }
+    if (s.fork) cudaEventDestroy(s.fork);
+    if (s.join) cudaEventDestroy(s.join);
   }
   cudaStreamSynchronize(P->side);
   for (auto& s : e->slots) {
@@ -544,12 +554,35 @@ sage_status wait_ready_enqueued(Entry* e) {
 
 bool valid_fn(sage_fn f) { return f && f->magic == kFnMagic && f->e; }
 
+// fp32 dense layer: tensor cores (3 x tf32) when the shape tiles (N multiple of 64,
+// 16-byte rows), otherwise the CUDA-core kernel.
+bool f32_on_tensor_cores(int N, int K, int ldx, int ldy) { return N % 64 == 0 && K % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0; }
+
+cudaError_t launch_f32_layer(int M, int N, int K, const float* x, int ldx, const float* W, const float* b, int relu,
+                             float* y, int ldy, int* err, cudaStream_t s) {
+  if (f32_on_tensor_cores(N, K, ldx, ldy)) return launch_linear_f32_tc(M, N, K, x, ldx, W, b, relu, y, ldy, err, s);
+  return launch_linear_f32(M, N, K, x, ldx, W, b, relu, y, ldy, s);
+}
+
+int f32_kind(int N, int K, int ldx, int ldy) {
+  return f32_on_tensor_cores(N, K, ldx, ldy) ? kProfGemmTf32 : kProfGemmF32;
+}
+
 sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t stream) {
   const int M = tab.M;
   const int nb = static_cast<int>(e->bot.size()), nt = static_cast<int>(e->top.size());
   const size_t es = e->elem();
   const int cd = e->concat_dim();
   char* bot_out = s.concat + static_cast<size_t>(e->T) * e->dim * es;
+  // fork: the bottom MLP (columns [T*dim, cd) of the concat buffer) runs on the
+  // slot's branch stream while the gather (columns [0, T*dim)) runs on `stream`
+  // (while kernel timing is on, the branch is serialised so that each kernel's
+  // events measure it alone)
+  const bool overlap = !g_prof_on.load(std::memory_order_relaxed);
+  SAGE_CK(cudaEventRecord(s.fork, stream));
+  SAGE_CK(cudaStreamWaitEvent(s.branch, s.fork, 0));
+  const cudaStream_t main_stream = stream;
+  if (overlap) stream = s.branch;
   // bottom MLP (layer 0 reads each invocation's dense rows)
   {
     const Layer& L0 = e->layers[0];
@@ -563,13 +596,16 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     const void* x = s.bot[l - 1];
     void* y = l == nb - 1 ? bot_out : s.bot[l];
     const int ldy = l == nb - 1 ? cd : e->bot[l];
-    ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : kProfGemmF32, 2.0 * M * L.in * L.out);
+    ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : f32_kind(L.out, L.in, L.in, ldy),
+                 2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
       SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, L.in, L.W, L.b, 1, y, ldy, e->d_err, stream));
     else
-      SAGE_CK(launch_linear_f32(M, L.out, L.in, static_cast<const float*>(x), L.in, static_cast<const float*>(L.W),
-                                L.b, 1, static_cast<float*>(y), ldy, stream));
+      SAGE_CK(launch_f32_layer(M, L.out, L.in, static_cast<const float*>(x), L.in, static_cast<const float*>(L.W),
+                               L.b, 1, static_cast<float*>(y), ldy, e->d_err, stream));
   }
+  SAGE_CK(cudaEventRecord(s.join, overlap ? s.branch : main_stream));
+  stream = main_stream;
   // embedding-bag gather into the concat columns [0, T*dim)
   {
     GatherArgs a;
@@ -592,19 +628,22 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     ProfScope ps(stream, kProfGather, lookups * (row + 4.0) + static_cast<double>(e->T) * M * (8.0 + row));
     SAGE_CK(launch_gather(a, tab, stream));
   }
+  // join: the top MLP needs both halves of the concat buffer
+  SAGE_CK(cudaStreamWaitEvent(stream, s.join, 0));
   // top MLP hidden layers
   const char* x = s.concat;
   int ldx = cd;
   for (int l = 0; l + 1 < nt; ++l) {
     const Layer& L = e->layers[nb + l];
     char* y = s.top[l];
-    ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : kProfGemmF32, 2.0 * M * L.in * L.out);
+    ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : f32_kind(L.out, L.in, ldx, L.out),
+                 2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
       SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, ldx, L.W, L.b, 1, y, L.out, e->d_err, stream));
     else
-      SAGE_CK(launch_linear_f32(M, L.out, L.in, reinterpret_cast<const float*>(x), ldx,
-                                static_cast<const float*>(L.W), L.b, 1, reinterpret_cast<float*>(y), L.out,
-                                stream));
+      SAGE_CK(launch_f32_layer(M, L.out, L.in, reinterpret_cast<const float*>(x), ldx,
+                               static_cast<const float*>(L.W), L.b, 1, reinterpret_cast<float*>(y), L.out,
+                               e->d_err, stream));
     x = y;
     ldx = L.out;
   }
@@ -889,6 +928,9 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     st = build_slot(e, s, e->max_batch, P->side);
     if (st != SAGE_OK) return setup_failed(st);
     ce = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "event: %s", cudaGetErrorString(ce)));
   }
   // allocations on the side stream must precede any use on other streams
@@ -1263,8 +1305,8 @@ sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, in
   if (dtype == SAGE_BF16)
     e = launch_linear_bf16_tc(M, N, K, x, ldx, W, bias, act, y, ldy, err_word, static_cast<cudaStream_t>(stream));
   else
-    e = launch_linear_f32(M, N, K, static_cast<const float*>(x), ldx, static_cast<const float*>(W), bias, act,
-                          static_cast<float*>(y), ldy, static_cast<cudaStream_t>(stream));
+    e = launch_f32_layer(M, N, K, static_cast<const float*>(x), ldx, static_cast<const float*>(W), bias, act,
+                         static_cast<float*>(y), ldy, err_word, static_cast<cudaStream_t>(stream));
   if (e == cudaErrorInvalidValue) return fail(SAGE_ERR_INVALID, "unsupported shape or alignment");
   SAGE_CK(e);
   return SAGE_OK;

@@ -51,6 +51,7 @@ static inline uint16_t wl_bf16_rne(float f) {
 }
 
 /* Fill n elements [first, first+n) of stream (seed, bound); dtype 0 = fp32, 1 = bf16. */
+__attribute__((target_clones("arch=x86-64-v4", "arch=x86-64-v3", "default")))
 void wl_fill_stream(void* dst, int dtype, uint64_t seed, float bound, uint64_t first, size_t n) {
     float step = bound / 8388608.0f;
     if (dtype == 0) {
