@@ -227,6 +227,14 @@ sage_status sage_invoke_batch(sage_fn fn, const sage_invocation* invs, int n, vo
  * returns after the outputs are in host memory. */
 sage_status sage_invoke_batch_host(sage_fn fn, const sage_host_invocation* invs, int n, void* stream);
 
+/* sage_invoke_batch_host without the final wait: enqueues the input copies, the
+ * fused batch and the output copies and returns.  The inputs are copied on the
+ * workspace slot's own copy stream, which waits only for that slot's previous
+ * batch, so with workspace_slots >= 2 consecutive calls overlap one batch's
+ * copies with the previous batch's compute.  The host buffers must stay valid,
+ * and the outputs may be read, only after `stream` has been synchronised. */
+sage_status sage_invoke_batch_host_async(sage_fn fn, const sage_host_invocation* invs, int n, void* stream);
+
 /* Read and clear the function's device error word after synchronising it:
  * SAGE_OK, SAGE_ERR_BOUNDS (a bag row index was outside its table; the row was
  * skipped) or SAGE_ERR_DEVICE (a kernel's bounded wait ran out). */
@@ -241,6 +249,15 @@ sage_status sage_release(sage_fn fn);
 sage_status sage_pool_destroy(sage_pool pool);
 
 sage_status sage_pool_stats_get(sage_pool pool, sage_pool_stats* out);
+
+/* Page-locked host memory for invocation buffers and host images: 2 MiB aligned,
+ * backed by transparent huge pages where the kernel allows, registered with
+ * cudaHostRegister (rounded up to 2 MiB).  Host->device copies from it run near
+ * the link rate even for buffers of a few MB, which small separately pinned
+ * allocations do not on hosts that map DMA through 4 KiB pages.  Free with
+ * sage_host_free. */
+sage_status sage_host_alloc(size_t bytes, void** out);
+sage_status sage_host_free(void* ptr);
 
 /* Thread-local message of the last error returned on this thread ("" if none). */
 const char* sage_last_error(void);
@@ -265,6 +282,17 @@ typedef struct {
 
 sage_status sage_profile_enable(int on);
 int sage_profile_read(sage_kernel_time* out, int max);
+
+/* ---- autotuning of the tensor-core GEMM tiles ----
+ * sage_autotune times every tile configuration (N tile x pipeline depth) of each
+ * tensor-core layer of `fn` for a batch of `rows` samples (bucketed to the next
+ * power of two) on scratch operands it allocates and frees, and records the
+ * fastest per shape in a process-wide table that every later launch of that
+ * shape uses.  Synchronous.  sage_tuning_save / _load write / read the table as
+ * text keyed by the GPU's name (entries for other GPUs are ignored on load). */
+sage_status sage_autotune(sage_fn fn, int rows, void* stream);
+sage_status sage_tuning_save(const char* path);
+sage_status sage_tuning_load(const char* path);
 
 /* ---- serving ----
  * sage_serve replays a trace of timed requests against several functions on the
@@ -365,6 +393,14 @@ sage_status sage_embedding_bag_sum(sage_dtype dtype, const void* tables, const i
  * needs K and N multiples of 64 and 16-byte aligned rows. */
 sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,
                         const float* bias, int act, void* y, int ldy, int* err_word, void* stream);
+
+/* sage_linear with an explicit tensor-core tile configuration: N tile `bn` and
+ * pipeline depth `stages` (0, 0 = automatic / tuned).  Configurations: BF16
+ * (256,4) (128,6) (64,8) (256,2) (128,3) (64,4); F32 on tensor cores (128,3)
+ * (64,4) (64,2).  SAGE_ERR_INVALID for other pairs or shapes they cannot tile. */
+sage_status sage_linear_tiled(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,
+                              const float* bias, int act, void* y, int ldy, int bn, int stages, int* err_word,
+                              void* stream);
 
 #ifdef __cplusplus
 }

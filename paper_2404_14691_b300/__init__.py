@@ -47,6 +47,36 @@ def profile_read() -> dict:
             for i in range(n)}
 
 
+class _HostBlock:
+    def __init__(self, nbytes: int):
+        p = ctypes.c_void_p()
+        check(lib().sage_host_alloc(int(nbytes), ctypes.byref(p)), "sage_host_alloc")
+        self.ptr = p.value
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().sage_host_free(self.ptr)
+            self.ptr = None
+
+
+def host_empty(shape, dtype):
+    """A numpy array in page-locked, huge-page-backed host memory (sage_host_alloc)."""
+    import numpy as np
+    dt = np.dtype(dtype)
+    n = int(np.prod(shape)) if np.ndim(shape) else int(shape)
+    blk = _HostBlock(max(1, n * dt.itemsize))
+    buf = (ctypes.c_char * max(1, n * dt.itemsize)).from_address(blk.ptr)
+    buf._block = blk  # the array's base (buf) keeps the block alive
+    return np.frombuffer(buf, dtype=dt, count=n).reshape(shape)
+
+
+def host_copy(a):
+    """A copy of numpy array `a` in memory from host_empty."""
+    out = host_empty(a.shape, a.dtype)
+    out[...] = a
+    return out
+
+
 def torch_allocator_hooks(device: int = 0):
     """(alloc, free) C callbacks routing the pool's device memory through PyTorch's
     caching allocator."""
@@ -104,6 +134,11 @@ def serve(pool: "Pool", functions: Sequence[dict], requests: Sequence[tuple], ma
     return out, {name: getattr(st, name) for name, _ in ServeStats._fields_}
 
 
+def host_invocations(invs: Sequence[tuple]):
+    """A reusable C array of sage_host_invocation from (batch, dense, indices, offsets, num_indices, out)."""
+    return (HostInvocation * len(invs))(*[HostInvocation(int(b), d, i, o, int(n), u) for (b, d, i, o, n, u) in invs])
+
+
 class Function:
     """A reference to a prepared function (sage_fn)."""
 
@@ -137,11 +172,23 @@ class Function:
         check(lib().sage_invoke_batch(self.handle, arr, len(invs), _stream_handle(stream)), "sage_invoke_batch")
 
     def invoke_batch_host(self, invs: Sequence[tuple], stream=None) -> None:
-        """invs: (batch, dense_ptr, indices_ptr, offsets_ptr, num_indices, out_ptr) per invocation (host pointers)."""
-        arr = (HostInvocation * len(invs))(*[HostInvocation(int(b), d, i, o, int(n), u)
-                                             for (b, d, i, o, n, u) in invs])
-        check(lib().sage_invoke_batch_host(self.handle, arr, len(invs), _stream_handle(stream)),
+        """invs: (batch, dense_ptr, indices_ptr, offsets_ptr, num_indices, out_ptr) per invocation (host
+        pointers), or an array built by host_invocations()."""
+        arr = invs if isinstance(invs, ctypes.Array) else host_invocations(invs)
+        check(lib().sage_invoke_batch_host(self.handle, arr, len(arr), _stream_handle(stream)),
               "sage_invoke_batch_host")
+
+    def autotune(self, rows: int, stream=None) -> None:
+        """Time the tile configurations of this function's tensor-core layers for a batch
+        of `rows` samples and keep the fastest (process-wide)."""
+        check(lib().sage_autotune(self.handle, int(rows), _stream_handle(stream)), "sage_autotune")
+
+    def invoke_batch_host_async(self, invs, stream=None) -> None:
+        """As invoke_batch_host without waiting; synchronise `stream` before reading outputs.
+        invs: a list of tuples, or an array built once by host_invocations()."""
+        arr = invs if isinstance(invs, ctypes.Array) else host_invocations(invs)
+        check(lib().sage_invoke_batch_host_async(self.handle, arr, len(arr), _stream_handle(stream)),
+              "sage_invoke_batch_host_async")
 
     def check_errors(self) -> None:
         """Raise SageError if a kernel saw an out-of-range row or a timed-out wait."""
@@ -187,6 +234,14 @@ class Pool:
             self.handle = None
 
 
+def tuning_save(path: str) -> None:
+    check(lib().sage_tuning_save(path.encode()), "sage_tuning_save")
+
+
+def tuning_load(path: str) -> None:
+    check(lib().sage_tuning_load(path.encode()), "sage_tuning_load")
+
+
 def embedding_bag_sum(dtype: int, tables: int, table_rows: Sequence[int], dim: int, batch: int, indices: int,
                       offsets: int, out: int, ldo: int, err_word: Optional[int] = None, stream=None) -> None:
     """sage_embedding_bag_sum on device pointers."""
@@ -197,7 +252,11 @@ def embedding_bag_sum(dtype: int, tables: int, table_rows: Sequence[int], dim: i
 
 
 def linear(dtype: int, M: int, N: int, K: int, x: int, ldx: int, W: int, bias: int, relu: bool, y: int, ldy: int,
-           err_word: Optional[int] = None, stream=None) -> None:
-    """sage_linear on device pointers."""
-    check(lib().sage_linear(dtype, M, N, K, x, ldx, W, bias, 1 if relu else 0, y, ldy, err_word,
-                            _stream_handle(stream)), "sage_linear")
+           err_word: Optional[int] = None, stream=None, tile=None) -> None:
+    """sage_linear on device pointers; tile=(bn, stages) pins the tensor-core tile configuration."""
+    if tile is None:
+        check(lib().sage_linear(dtype, M, N, K, x, ldx, W, bias, 1 if relu else 0, y, ldy, err_word,
+                                _stream_handle(stream)), "sage_linear")
+    else:
+        check(lib().sage_linear_tiled(dtype, M, N, K, x, ldx, W, bias, 1 if relu else 0, y, ldy, int(tile[0]),
+                                      int(tile[1]), err_word, _stream_handle(stream)), "sage_linear_tiled")

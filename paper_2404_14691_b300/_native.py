@@ -104,19 +104,26 @@ SIGNATURES = [
     ("sage_invoke", _i, [_vp, ctypes.POINTER(Invocation), _vp]),
     ("sage_invoke_batch", _i, [_vp, ctypes.POINTER(Invocation), _i, _vp]),
     ("sage_invoke_batch_host", _i, [_vp, ctypes.POINTER(HostInvocation), _i, _vp]),
+    ("sage_invoke_batch_host_async", _i, [_vp, ctypes.POINTER(HostInvocation), _i, _vp]),
     ("sage_fn_check", _i, [_vp]),
     ("sage_release", _i, [_vp]),
     ("sage_pool_destroy", _i, [_vp]),
     ("sage_pool_stats_get", _i, [_vp, ctypes.POINTER(PoolStats)]),
     ("sage_last_error", ctypes.c_char_p, []),
+    ("sage_host_alloc", _i, [_sz, ctypes.POINTER(_vp)]),
+    ("sage_host_free", _i, [_vp]),
     ("sage_kernel_launches", _i64, []),
     ("sage_profile_enable", _i, [_i]),
     ("sage_profile_read", _i, [ctypes.POINTER(KernelTime), _i]),
+    ("sage_autotune", _i, [_vp, _i, _vp]),
+    ("sage_tuning_save", _i, [ctypes.c_char_p]),
+    ("sage_tuning_load", _i, [ctypes.c_char_p]),
     ("sage_serve", _i, [_vp, ctypes.POINTER(FnDesc), _i, ctypes.POINTER(Request), _i, ctypes.POINTER(ServeConfig),
                         ctypes.POINTER(RequestResult), ctypes.POINTER(ServeStats)]),
     ("sage_invoke_noalloc", _i, [ctypes.POINTER(FnDesc), _vp, _vp, ctypes.POINTER(Invocation), _vp]),
     ("sage_embedding_bag_sum", _i, [_i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     ("sage_linear", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp]),
+    ("sage_linear_tiled", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _i, _i, _vp, _vp]),
 ]
 
 _lib = None

@@ -23,23 +23,22 @@ namespace sage {
 namespace {
 
 constexpr int kBM = 128, kBK = 64;
-constexpr int kPipeBytes = 192 * 1024;
 
-template <int BN>
+template <int BN, int NST>
 struct TcCfg {
   static constexpr int A_BYTES = kBM * kBK * 2;
   static constexpr int B_BYTES = BN * kBK * 2;
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int STAGES = kPipeBytes / STAGE;
+  static constexpr int STAGES = NST;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
 };
 
-template <int BN>
+template <int BN, int NST>
 __global__ void __launch_bounds__(128, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ Y, int ldy,
                    int* err) {
-  using C = TcCfg<BN>;
+  using C = TcCfg<BN, NST>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -140,23 +139,39 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int 
   return make_tmap_2d(m, 1, base, rows, cols, ld, kBK, box_rows);
 }
 
-template <int BN>
+template <int BN, int NST>
 cudaError_t launch_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias, int relu,
                       void* y, int ldy, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcCfg<BN>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TcCfg<BN, NST>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   CUtensorMap ta, tb;
   if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
   dim3 grid(N / BN, (M + kBM - 1) / kBM);
-  gemm_tc_kernel<BN><<<grid, 128, TcCfg<BN>::SMEM, s>>>(ta, tb, M, N, K, bias, relu,
-                                                       static_cast<__nv_bfloat16*>(y), ldy, err);
+  gemm_tc_kernel<BN, NST><<<grid, 128, TcCfg<BN, NST>::SMEM, s>>>(ta, tb, M, N, K, bias, relu,
+                                                                static_cast<__nv_bfloat16*>(y), ldy, err);
   count_launch();
   return cudaGetLastError();
+}
+
+// Tile shapes the bf16 GEMM can run: (BN, stages).  The deep pipelines use
+// 192 KB of shared memory (one CTA per SM); the shallow ones ~100 KB (two CTAs
+// per SM, so one CTA's epilogue overlaps the other's main loop).
+const GemmCfg kBf16Cfgs[] = {{256, 4}, {128, 6}, {64, 8}, {256, 2}, {128, 3}, {64, 4}};
+
+cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const void* x, int ldx, const void* W, const float* bias,
+                       int relu, void* y, int ldy, int* err, cudaStream_t s) {
+  if (c.bn == 256 && c.stages == 4) return launch_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 128 && c.stages == 6) return launch_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 64 && c.stages == 8) return launch_bn<64, 8>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 256 && c.stages == 2) return launch_bn<256, 2>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 128 && c.stages == 3) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 64 && c.stages == 4) return launch_bn<64, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  return cudaErrorInvalidValue;
 }
 
 int g_sms = 0;
@@ -193,14 +208,29 @@ bool make_tmap_2d(CUtensorMap* m, int dtype, const void* base, int rows, int col
 
 void preload_tc_kernels() {
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, gemm_tc_kernel<64>);
-  cudaFuncGetAttributes(&fa, gemm_tc_kernel<128>);
-  cudaFuncGetAttributes(&fa, gemm_tc_kernel<256>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<256, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<128, 6>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<64, 8>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<256, 2>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<128, 3>);
+  cudaFuncGetAttributes(&fa, gemm_tc_kernel<64, 4>);
   encode_fn();
 }
 
+int gemm_candidates(int kind, GemmCfg* out, int max) {
+  int n = 0;
+  if (kind == kGemmBf16) {
+    for (const GemmCfg& c : kBf16Cfgs)
+      if (n < max) out[n++] = c;
+  } else {
+    n = tf32_candidates(out, max);
+  }
+  return n;
+}
+
 cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, const void* W,
-                                  const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s) {
+                                  const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s,
+                                  GemmCfg cfg) {
   if (M <= 0) return cudaSuccess;
   if (K <= 0 || (K % kBK) || (N % 64) || (ldx % 8) || (ldy % 8) ||
       (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(W) & 15) ||
@@ -211,10 +241,14 @@ cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  if (cfg.bn) {
+    if (N % cfg.bn) return cudaErrorInvalidValue;
+    return launch_cfg(cfg, M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  }
   const int mt = (M + kBM - 1) / kBM;
-  if (N % 256 == 0 && mt * (N / 256) >= g_sms) return launch_bn<256>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
-  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
-  return launch_bn<64>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 256 == 0 && mt * (N / 256) >= g_sms) return launch_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  return launch_bn<64, 8>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
 }
 
 }  // namespace sage

@@ -24,14 +24,13 @@ namespace sage {
 namespace {
 
 constexpr int kBM = 128, kBK = 32;  // 32 fp32 = one 128-byte swizzle row
-constexpr int kPipeBytes = 192 * 1024;
 
-template <int BN>
+template <int BN, int NST>
 struct Tf32Cfg {
   static constexpr int A_BYTES = kBM * kBK * 4;  // 16 KB
   static constexpr int B_BYTES = BN * kBK * 4;
   static constexpr int STAGE = 2 * (A_BYTES + B_BYTES);  // hi + lo of both operands
-  static constexpr int STAGES = kPipeBytes / STAGE;
+  static constexpr int STAGES = NST;
   static constexpr int SMEM = STAGES * STAGE + 1024 + 512;
   static_assert(STAGES >= 2, "pipeline depth");
 };
@@ -58,12 +57,12 @@ __device__ __forceinline__ void split_tile(float* hi, float* lo, int nfloat, int
   }
 }
 
-template <int BN>
+template <int BN, int NST>
 __global__ void __launch_bounds__(192, 1)
     gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
                        int N, int K, const float* __restrict__ bias, int relu, float* __restrict__ Y, int ldy,
                        int* err) {
-  using C = Tf32Cfg<BN>;
+  using C = Tf32Cfg<BN, NST>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // per stage: A_hi | B_hi | A_lo | B_lo
@@ -186,13 +185,13 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
-template <int BN>
+template <int BN, int NST>
 cudaError_t launch_bn(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias, int relu,
                       float* y, int ldy, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Tf32Cfg<BN>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Tf32Cfg<BN, NST>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -200,9 +199,20 @@ cudaError_t launch_bn(int M, int N, int K, const float* x, int ldx, const float*
   if (!make_tmap_2d(&ta, 0, x, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tb, 0, W, N, K, K, kBK, BN))
     return cudaErrorInvalidValue;
   dim3 grid(N / BN, (M + kBM - 1) / kBM);
-  gemm_tf32x3_kernel<BN><<<grid, 192, Tf32Cfg<BN>::SMEM, s>>>(ta, tb, M, N, K, bias, relu, y, ldy, err);
+  gemm_tf32x3_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(ta, tb, M, N, K, bias, relu, y, ldy, err);
   count_launch();
   return cudaGetLastError();
+}
+
+// (BN, stages): deep pipelines at 1 CTA per SM, shallow ones at 2 CTAs per SM.
+const GemmCfg kTf32Cfgs[] = {{128, 3}, {64, 4}, {64, 2}};
+
+cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
+                       int relu, float* y, int ldy, int* err, cudaStream_t s) {
+  if (c.bn == 128 && c.stages == 3) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 64 && c.stages == 4) return launch_bn<64, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 64 && c.stages == 2) return launch_bn<64, 2>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  return cudaErrorInvalidValue;
 }
 
 int g_sms = 0;
@@ -211,12 +221,20 @@ int g_sms = 0;
 
 void preload_tf32_kernels() {
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64>);
-  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<128>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<128, 3>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64, 2>);
+}
+
+int tf32_candidates(GemmCfg* out, int max) {
+  int n = 0;
+  for (const GemmCfg& c : kTf32Cfgs)
+    if (n < max) out[n++] = c;
+  return n;
 }
 
 cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
-                                 int relu, float* y, int ldy, int* err, cudaStream_t s) {
+                                 int relu, float* y, int ldy, int* err, cudaStream_t s, GemmCfg cfg) {
   if (M <= 0) return cudaSuccess;
   if (K <= 0 || (K % 4) || (N % 64) || (ldx % 4) || (ldy % 4) || (reinterpret_cast<uintptr_t>(x) & 15) ||
       (reinterpret_cast<uintptr_t>(W) & 15) || (reinterpret_cast<uintptr_t>(y) & 15))
@@ -226,9 +244,13 @@ cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, c
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  if (cfg.bn) {
+    if (N % cfg.bn) return cudaErrorInvalidValue;
+    return launch_cfg(cfg, M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  }
   const int mt = (M + kBM - 1) / kBM;
-  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
-  return launch_bn<64>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  return launch_bn<64, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
 }
 
 }  // namespace sage

@@ -50,14 +50,29 @@ cudaError_t launch_head(int dtype, const InvTable& tab, int K, const void* h, in
 bool make_tmap_2d(CUtensorMap* m, int dtype, const void* base, int rows, int cols, int ld, int box_cols,
                   int box_rows);
 
+// Tile configuration of a tensor-core GEMM launch: N tile and pipeline depth;
+// {0, 0} lets the launcher choose by its shape heuristic.
+struct GemmCfg {
+  int bn;
+  int stages;
+};
+enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2 };
+int gemm_candidates(int kind, GemmCfg* out, int max);
+int tf32_candidates(GemmCfg* out, int max);
+// Tuned configuration for a GEMM shape ({0, 0} if none was tuned).
+GemmCfg tuned_gemm(int kind, int M, int N, int K);
+// Times every configuration of one shape and records the fastest.
+sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg* chosen, double* best_ms);
+
 // Dense layers y = act(x W^T + b).
 cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
                               int relu, float* y, int ldy, cudaStream_t s);
 cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, const void* W,
-                                  const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s);
+                                  const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s,
+                                  GemmCfg cfg = GemmCfg{0, 0});
 // fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.
 cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
-                                 int relu, float* y, int ldy, int* err, cudaStream_t s);
+                                 int relu, float* y, int ldy, int* err, cudaStream_t s, GemmCfg cfg = GemmCfg{0, 0});
 
 // Kernel loading: query every kernel of a translation unit once, which makes the
 // CUDA runtime load its module (lazy loading defers this to first use).

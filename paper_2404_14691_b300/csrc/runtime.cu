@@ -6,7 +6,9 @@
 // and the invocation chain of the recommendation-style function.
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <atomic>
@@ -66,6 +68,35 @@ double ms_since(Clock::time_point t0) {
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------- pinned host memory
+// Host memory the copy engines read fast: 2 MiB aligned, advised to transparent
+// huge pages, then page-locked with cudaHostRegister.  (Small separate pinned
+// allocations backed by 4 KiB pages copied at ~10 GB/s on the B300 hosts
+// measured, slices of huge-page-backed memory at ~50 GB/s.)
+constexpr size_t kHugePage = size_t(2) << 20;
+
+void* host_alloc_pinned(size_t bytes, cudaError_t* err) {
+  bytes = (bytes + kHugePage - 1) & ~(kHugePage - 1);
+  void* p = nullptr;
+  if (posix_memalign(&p, kHugePage, bytes) != 0 || !p) {
+    *err = cudaErrorMemoryAllocation;
+    return nullptr;
+  }
+  madvise(p, bytes, MADV_HUGEPAGE);
+  *err = cudaHostRegister(p, bytes, cudaHostRegisterDefault);
+  if (*err != cudaSuccess) {
+    free(p);
+    return nullptr;
+  }
+  return p;
+}
+
+void host_free_pinned(void* p) {
+  if (!p) return;
+  cudaHostUnregister(p);
+  free(p);
+}
 
 // ---------------------------------------------------------------- host workers
 // A fixed set of threads that run fn(i) for i in [0, n) together with the caller.
@@ -161,6 +192,10 @@ struct Slot {
   // the bottom MLP runs on `branch` beside the gather (fork / join events)
   cudaStream_t branch = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // host invocations: inputs are copied on `h2d` (after the slot's previous use)
+  // so that they overlap the compute still running on the launch stream
+  cudaStream_t h2d = nullptr;
+  cudaEvent_t copied = nullptr;
 };
 
 }  // namespace
@@ -218,8 +253,10 @@ struct sage_pool_s {
   sage_dev_free_fn dfree = nullptr;
   void* actx = nullptr;
   bool serial_setup = false;
-  cudaStream_t side = nullptr;
+  cudaStream_t side = nullptr;   // staging copies
+  cudaStream_t alloc = nullptr;  // allocations and frees (never waits behind staging copies)
   size_t chunk_bytes = 0;
+  char* ring_mem = nullptr;  // one pinned, huge-page-backed allocation for all chunks
   std::vector<char*> ring;
   std::vector<cudaEvent_t> ring_ev;
   size_t ring_next = 0;
@@ -525,16 +562,21 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
     }
     if (s.fork) cudaEventDestroy(s.fork);
     if (s.join) cudaEventDestroy(s.join);
+    if (s.h2d) {
+      cudaStreamSynchronize(s.h2d);
+      cudaStreamDestroy(s.h2d);
+    }
+    if (s.copied) cudaEventDestroy(s.copied);
   }
-  cudaStreamSynchronize(P->side);
+  // every use of the entry's memory has finished (ready + slot events above)
   for (auto& s : e->slots) {
-    P->dev_free(s.buf, s.bytes, P->side);
-    P->dev_free(s.io, s.io_bytes, P->side);
+    P->dev_free(s.buf, s.bytes, P->alloc);
+    P->dev_free(s.io, s.io_bytes, P->alloc);
   }
-  P->dev_free(e->d_tables, e->tables_bytes, P->side);
-  P->dev_free(e->d_weights, e->weights_bytes, P->side);
-  P->dev_free(e->d_err, 256, P->side);
-  cudaStreamSynchronize(P->side);
+  P->dev_free(e->d_tables, e->tables_bytes, P->alloc);
+  P->dev_free(e->d_weights, e->weights_bytes, P->alloc);
+  P->dev_free(e->d_err, 256, P->alloc);
+  cudaStreamSynchronize(P->alloc);
   if (e->ready) cudaEventDestroy(e->ready);
   {
     std::lock_guard<std::mutex> g(P->mu);
@@ -560,7 +602,8 @@ bool f32_on_tensor_cores(int N, int K, int ldx, int ldy) { return N % 64 == 0 &&
 
 cudaError_t launch_f32_layer(int M, int N, int K, const float* x, int ldx, const float* W, const float* b, int relu,
                              float* y, int ldy, int* err, cudaStream_t s) {
-  if (f32_on_tensor_cores(N, K, ldx, ldy)) return launch_linear_f32_tc(M, N, K, x, ldx, W, b, relu, y, ldy, err, s);
+  if (f32_on_tensor_cores(N, K, ldx, ldy))
+    return launch_linear_f32_tc(M, N, K, x, ldx, W, b, relu, y, ldy, err, s, tuned_gemm(kGemmTf32x3, M, N, K));
   return launch_linear_f32(M, N, K, x, ldx, W, b, relu, y, ldy, s);
 }
 
@@ -599,7 +642,8 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : f32_kind(L.out, L.in, L.in, ldy),
                  2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
-      SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, L.in, L.W, L.b, 1, y, ldy, e->d_err, stream));
+      SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, L.in, L.W, L.b, 1, y, ldy, e->d_err, stream,
+                                    tuned_gemm(kGemmBf16, M, L.out, L.in)));
     else
       SAGE_CK(launch_f32_layer(M, L.out, L.in, static_cast<const float*>(x), L.in, static_cast<const float*>(L.W),
                                L.b, 1, static_cast<float*>(y), ldy, e->d_err, stream));
@@ -639,7 +683,8 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : f32_kind(L.out, L.in, ldx, L.out),
                  2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
-      SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, ldx, L.W, L.b, 1, y, L.out, e->d_err, stream));
+      SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, ldx, L.W, L.b, 1, y, L.out, e->d_err, stream,
+                                    tuned_gemm(kGemmBf16, M, L.out, L.in)));
     else
       SAGE_CK(launch_f32_layer(M, L.out, L.in, reinterpret_cast<const float*>(x), ldx,
                                static_cast<const float*>(L.W), L.b, 1, reinterpret_cast<float*>(y), L.out,
@@ -703,6 +748,19 @@ extern "C" {
 
 const char* sage_last_error(void) { return t_err.c_str(); }
 
+sage_status sage_host_alloc(size_t bytes, void** out) {
+  if (!out || bytes == 0) return fail(SAGE_ERR_INVALID, "bad host allocation request");
+  cudaError_t e = cudaSuccess;
+  *out = host_alloc_pinned(bytes, &e);
+  if (!*out) return fail(SAGE_ERR_NOMEM, "pinned host allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+  return SAGE_OK;
+}
+
+sage_status sage_host_free(void* p) {
+  host_free_pinned(p);
+  return SAGE_OK;
+}
+
 int64_t sage_kernel_launches(void) { return sage::launches(); }
 
 sage_status sage_profile_enable(int on) {
@@ -764,10 +822,16 @@ sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
   P->chunk_bytes = c.staging_chunk_bytes ? ((c.staging_chunk_bytes + 4095) & ~size_t(4095)) : (size_t(64) << 20);
   const int nchunks = c.staging_chunks > 0 ? c.staging_chunks : 4;
   SAGE_CK(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+  SAGE_CK(cudaStreamCreateWithFlags(&P->alloc, cudaStreamNonBlocking));
+  {
+    cudaError_t he = cudaSuccess;
+    P->ring_mem = static_cast<char*>(host_alloc_pinned(P->chunk_bytes * nchunks, &he));
+    if (!P->ring_mem)
+      return fail(SAGE_ERR_NOMEM, "pinned staging ring of %zu bytes: %s", P->chunk_bytes * nchunks,
+                  cudaGetErrorString(he));
+  }
   for (int i = 0; i < nchunks; ++i) {
-    void* h = nullptr;
-    SAGE_CK(cudaHostAlloc(&h, P->chunk_bytes, cudaHostAllocDefault));
-    P->ring.push_back(static_cast<char*>(h));
+    P->ring.push_back(P->ring_mem + static_cast<size_t>(i) * P->chunk_bytes);
     cudaEvent_t ev;
     SAGE_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     SAGE_CK(cudaEventRecord(ev, P->side));
@@ -864,10 +928,13 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     e->ready = nullptr;
     return setup_failed(fail(SAGE_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce)));
   }
-  e->d_tables = static_cast<char*>(P->dev_alloc(e->tables_bytes, P->side));
-  e->d_weights = static_cast<char*>(P->dev_alloc(e->weights_bytes, P->side));
+  e->d_tables = static_cast<char*>(P->dev_alloc(e->tables_bytes, P->alloc));
+  e->d_weights = static_cast<char*>(P->dev_alloc(e->weights_bytes, P->alloc));
   if (!e->d_tables || !e->d_weights)
     return setup_failed(fail(SAGE_ERR_NOMEM, "device allocation of the read-only data of '%s' failed", d->fn_key));
+  // the staging copies (side stream) may target the slab only once it exists
+  ce = cudaStreamSynchronize(P->alloc);
+  if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "allocation: %s", cudaGetErrorString(ce)));
   {
     int64_t o = 0;
     for (int t = 0; t < e->T; ++t) {
@@ -920,22 +987,23 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
       e->layers.push_back({p.first, p.second, W, b});
     }
   }
-  e->d_err = static_cast<int*>(P->dev_alloc(256, P->side));
+  e->d_err = static_cast<int*>(P->dev_alloc(256, P->alloc));
   if (!e->d_err) return setup_failed(fail(SAGE_ERR_NOMEM, "error word allocation failed"));
-  ce = cudaMemsetAsync(e->d_err, 0, 256, P->side);
+  ce = cudaMemsetAsync(e->d_err, 0, 256, P->alloc);
   if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "memset: %s", cudaGetErrorString(ce)));
   for (auto& s : e->slots) {
-    st = build_slot(e, s, e->max_batch, P->side);
+    st = build_slot(e, s, e->max_batch, P->alloc);
     if (st != SAGE_OK) return setup_failed(st);
     ce = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.h2d, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming);
     if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "event: %s", cudaGetErrorString(ce)));
   }
   // allocations on the side stream must precede any use on other streams
-  ce = cudaEventRecord(e->slots[0].done, P->side);
-  if (ce == cudaSuccess) ce = cudaEventSynchronize(e->slots[0].done);
+  ce = cudaStreamSynchronize(P->alloc);
   if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "setup sync: %s", cudaGetErrorString(ce)));
   const double ws_ms = ms_since(tw);
   {
@@ -1083,6 +1151,9 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
       sl->io = static_cast<char*>(e->pool->dev_alloc(nb, s));
       sl->io_bytes = sl->io ? nb : 0;
       if (!sl->io) return fail(SAGE_ERR_NOMEM, "host-invocation arena of %zu bytes", nb);
+      // the copy stream may use the new arena only after its allocation on `s`
+      SAGE_CK(cudaEventRecord(sl->copied, s));
+      SAGE_CK(cudaStreamWaitEvent(sl->h2d, sl->copied, 0));
     }
     char* pd = sl->io;
     char* pi = pd + align256(nd);
@@ -1135,7 +1206,10 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
     for (auto& r : dense_r) add(r.dst, r.src, r.n);
     for (auto& r : idx_r) add(r.dst, r.src, r.n);
     for (auto& r : off_r) add(r.dst, r.src, r.n);
-    for (auto& r : runs) SAGE_CK(cudaMemcpyAsync(r.dst, r.src, r.n, cudaMemcpyHostToDevice, s));
+    if (sl->used) SAGE_CK(cudaStreamWaitEvent(sl->h2d, sl->done, 0));
+    for (auto& r : runs) SAGE_CK(cudaMemcpyAsync(r.dst, r.src, r.n, cudaMemcpyHostToDevice, sl->h2d));
+    SAGE_CK(cudaEventRecord(sl->copied, sl->h2d));
+    SAGE_CK(cudaStreamWaitEvent(s, sl->copied, 0));
     SAGE_CK(cudaStreamWaitEvent(s, e->ready, 0));
     st = launch_chain(e, *sl, *tab, s);
     if (st != SAGE_OK) return st;
@@ -1165,6 +1239,16 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
 
 extern "C" {
 
+sage_status sage_invoke_batch_host_async(sage_fn f, const sage_host_invocation* invs, int n, void* stream) {
+  if (n < 0 || (n > 0 && !invs)) return fail(SAGE_ERR_INVALID, "bad invocation list");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; i += kMaxInv) {
+    sage_status st = sage::host_batch_async(f, invs + i, std::min(kMaxInv, n - i), s, -1);
+    if (st != SAGE_OK) return st;
+  }
+  return SAGE_OK;
+}
+
 sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, int n, void* stream) {
   if (n < 0 || (n > 0 && !invs)) return fail(SAGE_ERR_INVALID, "bad invocation list");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1176,6 +1260,29 @@ sage_status sage_invoke_batch_host(sage_fn f, const sage_host_invocation* invs, 
   return SAGE_OK;
 }
 
+
+sage_status sage_autotune(sage_fn f, int rows, void* stream) {
+  if (!valid_fn(f) || rows < 1) return fail(SAGE_ERR_INVALID, "bad autotune arguments");
+  Entry* e = f->e;
+  SAGE_CK(cudaSetDevice(e->pool->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int nb = static_cast<int>(e->bot.size()), nl = static_cast<int>(e->layers.size());
+  for (int l = 1; l + 1 < nl; ++l) {
+    const Layer& L = e->layers[l];
+    int kind = 0;
+    if (e->dtype == SAGE_BF16) {
+      kind = kGemmBf16;
+    } else {
+      const int ldx = l < nb ? L.in : (l == nb ? e->concat_dim() : L.in);
+      const int ldy = l == nb - 1 ? e->concat_dim() : L.out;
+      if (f32_on_tensor_cores(L.out, L.in, ldx, ldy)) kind = kGemmTf32x3;
+    }
+    if (!kind) continue;
+    sage_status st = autotune_gemm(kind, rows, L.out, L.in, s, nullptr, nullptr);
+    if (st != SAGE_OK) return st;
+  }
+  return SAGE_OK;
+}
 
 sage_status sage_fn_check(sage_fn f) {
   if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
@@ -1234,11 +1341,13 @@ sage_status sage_pool_destroy(sage_pool P) {
   if (P->stager.joinable()) P->stager.join();
   cudaSetDevice(P->device);
   cudaStreamSynchronize(P->side);
+  cudaStreamSynchronize(P->alloc);
   for (size_t i = 0; i < P->ring.size(); ++i) {
     cudaEventDestroy(P->ring_ev[i]);
-    cudaFreeHost(P->ring[i]);
   }
+  host_free_pinned(P->ring_mem);
   cudaStreamDestroy(P->side);
+  cudaStreamDestroy(P->alloc);
   P->workers.reset();
   delete P;
   return SAGE_OK;
@@ -1303,10 +1412,36 @@ sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, in
   if (M < 0 || N < 1 || K < 1 || !x || !W || !bias || !y) return fail(SAGE_ERR_INVALID, "bad linear arguments");
   cudaError_t e;
   if (dtype == SAGE_BF16)
-    e = launch_linear_bf16_tc(M, N, K, x, ldx, W, bias, act, y, ldy, err_word, static_cast<cudaStream_t>(stream));
+    e = launch_linear_bf16_tc(M, N, K, x, ldx, W, bias, act, y, ldy, err_word, static_cast<cudaStream_t>(stream),
+                              tuned_gemm(kGemmBf16, M, N, K));
   else
     e = launch_f32_layer(M, N, K, static_cast<const float*>(x), ldx, static_cast<const float*>(W), bias, act,
                          static_cast<float*>(y), ldy, err_word, static_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return fail(SAGE_ERR_INVALID, "unsupported shape or alignment");
+  SAGE_CK(e);
+  return SAGE_OK;
+}
+
+sage_status sage_linear_tiled(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,
+                              const float* bias, int act, void* y, int ldy, int bn, int stages, int* err_word,
+                              void* stream) {
+  if (bn == 0 && stages == 0) return sage_linear(dtype, M, N, K, x, ldx, W, bias, act, y, ldy, err_word, stream);
+  if (M < 0 || N < 1 || K < 1 || !x || !W || !bias || !y) return fail(SAGE_ERR_INVALID, "bad linear arguments");
+  GemmCfg cands[16];
+  const int nc = gemm_candidates(dtype == SAGE_BF16 ? kGemmBf16 : kGemmTf32x3, cands, 16);
+  bool known = false;
+  for (int c = 0; c < nc; ++c) known |= cands[c].bn == bn && cands[c].stages == stages;
+  if (!known) return fail(SAGE_ERR_INVALID, "unknown tile configuration (%d, %d)", bn, stages);
+  cudaError_t e;
+  if (dtype == SAGE_BF16)
+    e = launch_linear_bf16_tc(M, N, K, x, ldx, W, bias, act, y, ldy, err_word, static_cast<cudaStream_t>(stream),
+                              GemmCfg{bn, stages});
+  else if (f32_on_tensor_cores(N, K, ldx, ldy))
+    e = launch_linear_f32_tc(M, N, K, static_cast<const float*>(x), ldx, static_cast<const float*>(W), bias, act,
+                             static_cast<float*>(y), ldy, err_word, static_cast<cudaStream_t>(stream),
+                             GemmCfg{bn, stages});
+  else
+    return fail(SAGE_ERR_INVALID, "shape does not tile on the tensor cores");
   if (e == cudaErrorInvalidValue) return fail(SAGE_ERR_INVALID, "unsupported shape or alignment");
   SAGE_CK(e);
   return SAGE_OK;

@@ -1,0 +1,170 @@
+// Autotuner of the tensor-core GEMM tiles.
+//
+// For a GEMM shape (kind, M bucket, N, K) it times every tile configuration the
+// kernels offer (N tile x pipeline depth) on scratch operands with CUDA events
+// and keeps the fastest in a process-wide table; launches then use the table.
+// M is bucketed to the next power of two (>= 128), since the best tile depends
+// on how many waves of CTAs the batch makes.  The table can be saved to and
+// loaded from a text file keyed by the GPU's name, so a box tunes once.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/sage.h"
+#include "kernels.h"
+
+namespace sage {
+namespace {
+
+using Key = std::tuple<int, int, int, int>;  // kind, M bucket, N, K
+std::mutex g_mu;
+std::map<Key, GemmCfg> g_table;
+
+int bucket(int M) {
+  int b = 128;
+  while (b < M && b < (1 << 30)) b <<= 1;
+  return b;
+}
+
+std::string gpu_name() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return "unknown";
+  std::string s = p.name;
+  std::replace(s.begin(), s.end(), ' ', '_');
+  return s;
+}
+
+}  // namespace
+
+GemmCfg tuned_gemm(int kind, int M, int N, int K) {
+  std::lock_guard<std::mutex> g(g_mu);
+  auto it = g_table.find(Key{kind, bucket(M), N, K});
+  return it == g_table.end() ? GemmCfg{0, 0} : it->second;
+}
+
+// Times each candidate for one shape; returns the chosen config (or {0,0}).
+sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg* chosen, double* best_ms) {
+  const int Mb = bucket(M);
+  const size_t es = kind == kGemmBf16 ? 2 : 4;
+  void *x = nullptr, *w = nullptr, *y = nullptr, *b = nullptr;
+  int* err = nullptr;
+  auto cleanup = [&] {
+    cudaFree(x);
+    cudaFree(w);
+    cudaFree(y);
+    cudaFree(b);
+    cudaFree(err);
+  };
+  if (cudaMalloc(&x, static_cast<size_t>(Mb) * K * es) != cudaSuccess ||
+      cudaMalloc(&w, static_cast<size_t>(N) * K * es) != cudaSuccess ||
+      cudaMalloc(&y, static_cast<size_t>(Mb) * N * es) != cudaSuccess ||
+      cudaMalloc(&b, static_cast<size_t>(N) * 4) != cudaSuccess || cudaMalloc(&err, 256) != cudaSuccess) {
+    cleanup();
+    cudaGetLastError();
+    set_last_error("autotune: scratch allocation failed");
+    return SAGE_ERR_NOMEM;
+  }
+  // small nonzero operands (0x3c3c.. patterns), zero bias
+  cudaMemsetAsync(x, 0x3c, static_cast<size_t>(Mb) * K * es, s);
+  cudaMemsetAsync(w, 0x3c, static_cast<size_t>(N) * K * es, s);
+  cudaMemsetAsync(b, 0, static_cast<size_t>(N) * 4, s);
+  cudaMemsetAsync(err, 0, 256, s);
+  GemmCfg cands[16];
+  const int nc = gemm_candidates(kind, cands, 16);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  GemmCfg best{0, 0};
+  float best_t = 1e30f;
+  for (int c = 0; c < nc; ++c) {
+    if (N % cands[c].bn) continue;
+    auto run = [&] {
+      return kind == kGemmBf16
+                 ? launch_linear_bf16_tc(Mb, N, K, x, K, w, static_cast<float*>(b), 1, y, N, err, s, cands[c])
+                 : launch_linear_f32_tc(Mb, N, K, static_cast<float*>(x), K, static_cast<float*>(w),
+                                        static_cast<float*>(b), 1, static_cast<float*>(y), N, err, s, cands[c]);
+    };
+    if (run() != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    std::vector<float> t;
+    for (int r = 0; r < 5; ++r) {
+      cudaEventRecord(e0, s);
+      run();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    if (t[2] < best_t) {
+      best_t = t[2];
+      best = cands[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  cleanup();
+  if (ce != cudaSuccess) {
+    set_last_error("autotune: a timing run failed");
+    return SAGE_ERR_CUDA;
+  }
+  if (best.bn) {
+    std::lock_guard<std::mutex> g(g_mu);
+    g_table[Key{kind, Mb, N, K}] = best;
+  }
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = best_t;
+  return SAGE_OK;
+}
+
+}  // namespace sage
+
+extern "C" sage_status sage_tuning_save(const char* path) {
+  if (!path) return sage::set_last_error("null path"), SAGE_ERR_INVALID;
+  FILE* f = fopen(path, "w");
+  if (!f) return sage::set_last_error("cannot write the tuning file"), SAGE_ERR_INVALID;
+  const std::string gpu = sage::gpu_name();
+  std::lock_guard<std::mutex> g(sage::g_mu);
+  fprintf(f, "# gpu kind m_bucket N K bn stages\n");
+  for (auto& kv : sage::g_table)
+    fprintf(f, "%s %d %d %d %d %d %d\n", gpu.c_str(), std::get<0>(kv.first), std::get<1>(kv.first),
+            std::get<2>(kv.first), std::get<3>(kv.first), kv.second.bn, kv.second.stages);
+  fclose(f);
+  return SAGE_OK;
+}
+
+extern "C" sage_status sage_tuning_load(const char* path) {
+  if (!path) return sage::set_last_error("null path"), SAGE_ERR_INVALID;
+  FILE* f = fopen(path, "r");
+  if (!f) return sage::set_last_error("cannot read the tuning file"), SAGE_ERR_INVALID;
+  const std::string gpu = sage::gpu_name();
+  char line[512], name[256];
+  int kind, mb, n, k, bn, st, loaded = 0;
+  std::lock_guard<std::mutex> g(sage::g_mu);
+  while (fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    if (sscanf(line, "%255s %d %d %d %d %d %d", name, &kind, &mb, &n, &k, &bn, &st) != 7) continue;
+    if (gpu != name) continue;  // tuned on another GPU model
+    sage::GemmCfg cands[16];
+    const int nc = sage::gemm_candidates(kind, cands, 16);
+    bool known = false;
+    for (int c = 0; c < nc; ++c) known |= cands[c].bn == bn && cands[c].stages == st;
+    if (!known) continue;
+    sage::g_table[sage::Key{kind, mb, n, k}] = sage::GemmCfg{bn, st};
+    ++loaded;
+  }
+  fclose(f);
+  return loaded > 0 ? SAGE_OK : (sage::set_last_error("no entries for this GPU"), SAGE_ERR_INVALID);
+}

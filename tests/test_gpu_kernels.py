@@ -209,3 +209,53 @@ def test_linear_rejects_unsupported_shapes():
     with pytest.raises(sage.SageError):
         sage.linear(sage.SAGE_BF16, 4, 64, 100, x.data_ptr(), 100, W.data_ptr(), b.data_ptr(), False,
                     y.data_ptr(), 64)
+
+
+BF16_TILES = [(256, 4), (128, 6), (64, 8), (256, 2), (128, 3), (64, 4)]
+F32_TILES = [(128, 3), (64, 4), (64, 2)]
+
+
+@pytest.mark.parametrize("tile", BF16_TILES)
+def test_every_bf16_tile_configuration_matches_oracle(tile):
+    torch = _torch()
+    M, N, K = 700, 512, 1024
+    x, W, b = _bf16_case(M, N, K, 17)
+    xd, Wd, bd = bf16_dev(x), bf16_dev(W), dev(b)
+    y = torch.full((M, N), float("nan"), dtype=torch.bfloat16, device="cuda")
+    sage.linear(sage.SAGE_BF16, M, N, K, xd.data_ptr(), K, Wd.data_ptr(), bd.data_ptr(), True, y.data_ptr(), N,
+                tile=tile)
+    ref_y = torch.empty_like(y)
+    sage.linear(sage.SAGE_BF16, M, N, K, xd.data_ptr(), K, Wd.data_ptr(), bd.data_ptr(), True, ref_y.data_ptr(), N,
+                tile=BF16_TILES[0])
+    torch.cuda.synchronize()
+    ref, mag = oracle.linear(x, W, b, True, xmag=np.abs(x))
+    c = oracle.check_close(to_f64(y), ref, mag, RTOL["bf16"])
+    assert c["ok"] and c["max_scaled_err"] < 5e-3, c
+    assert torch.equal(y, ref_y)          # the tile shape does not change any output bit
+
+
+@pytest.mark.parametrize("tile", F32_TILES)
+def test_every_f32_tile_configuration_matches_oracle(tile):
+    torch = _torch()
+    M, N, K = 900, 256, 576
+    rng = np.random.default_rng(23)
+    x = rng.standard_normal((M, K)).astype(np.float32)
+    W = (rng.standard_normal((N, K)) / np.sqrt(K)).astype(np.float32)
+    b = rng.standard_normal(N).astype(np.float32)
+    xd, Wd, bd = dev(x), dev(W), dev(b)
+    y = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    sage.linear(sage.SAGE_F32, M, N, K, xd.data_ptr(), K, Wd.data_ptr(), bd.data_ptr(), False, y.data_ptr(), N,
+                tile=tile)
+    torch.cuda.synchronize()
+    ref, mag = oracle.linear(x, W, b, False, xmag=np.abs(x))
+    c = oracle.check_close(to_f64(y), ref, mag, RTOL["f32"])
+    assert c["ok"] and c["max_scaled_err"] < 2e-6, c
+
+
+def test_unknown_tile_configuration_is_rejected():
+    torch = _torch()
+    x = torch.zeros((4, 64), dtype=torch.bfloat16, device="cuda")
+    b = torch.zeros(64, device="cuda")
+    with pytest.raises(sage.SageError):
+        sage.linear(sage.SAGE_BF16, 4, 64, 64, x.data_ptr(), 64, x.data_ptr(), b.data_ptr(), False, x.data_ptr(), 64,
+                    tile=(96, 3))

@@ -284,3 +284,69 @@ def test_serial_and_parallel_setup_agree(serial):
         f.release()
     finally:
         p.destroy()
+
+
+def test_autotune_keeps_results_bitwise_and_tuning_file_roundtrips(pool, tmp_path):
+    torch = _torch()
+    for dtype in ("f32", "bf16"):
+        spec = spec_small(dtype, key="rt_tune_" + dtype)
+        f = prepare(pool, spec)
+        try:
+            invs = [workload.make_invocation(spec, B, seed=400 + i) for i, B in enumerate([700, 900])]
+            before = [DevInvocation(v) for v in invs]
+            f.invoke_batch([d.args() for d in before])
+            f.autotune(1600)
+            after = [DevInvocation(v) for v in invs]
+            f.invoke_batch([d.args() for d in after])
+            torch.cuda.synchronize()
+            for a, b in zip(before, after):
+                assert torch.equal(a.out, b.out)
+        finally:
+            f.release()
+    path = str(tmp_path / "tuning.txt")
+    sage.tuning_save(path)
+    lines = [l for l in open(path) if not l.startswith("#")]
+    assert len(lines) >= 3
+    sage.tuning_load(path)
+
+
+def test_async_host_batches_overlap_and_match(pool):
+    """Consecutive asynchronous host batches (alternating slots) give the device-path results."""
+    torch = _torch()
+    spec = spec_small("f32", key="rt_hasync")
+    fn = prepare(pool, spec, workspace_slots=2)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=500 + i) for i, B in enumerate([40, 300, 7, 128])]
+        devs = [DevInvocation(v) for v in invs]
+        fn.invoke_batch([d.args() for d in devs])
+        outs = [[np.full(v["batch"], np.nan, np.float32) for v in invs] for _ in range(5)]
+        stream = torch.cuda.Stream()
+        for k in range(5):
+            fn.invoke_batch_host_async([(v["batch"], v["dense"].ctypes.data, v["indices"].ctypes.data,
+                                         v["offsets"].ctypes.data, v["indices"].size, o.ctypes.data)
+                                        for v, o in zip(invs, outs[k])], stream=stream)
+        stream.synchronize()
+        for k in range(5):
+            for o, d in zip(outs[k], devs):
+                assert np.array_equal(o, d.out[:d.batch].cpu().numpy())
+    finally:
+        fn.release()
+
+
+def test_host_allocator_buffers_serve_host_invocations(pool):
+    """sage_host_alloc memory (page-locked, huge-page backed) as invocation buffers."""
+    spec = spec_small("bf16", key="rt_hostalloc")
+    fn = prepare(pool, spec)
+    try:
+        v = workload.make_invocation(spec, 200, seed=9)
+        hv = {k: sage.host_copy(v[k]) for k in ("dense", "indices", "offsets")}
+        assert all(np.array_equal(hv[k], v[k]) for k in hv)
+        out = sage.host_empty(200, np.float32)
+        fn.invoke_batch_host([(200, hv["dense"].ctypes.data, hv["indices"].ctypes.data, hv["offsets"].ctypes.data,
+                               v["indices"].size, out.ctypes.data)])
+        d = DevInvocation(v)
+        fn.invoke(*d.args())
+        _torch().cuda.synchronize()
+        assert np.array_equal(out, d.out.cpu().numpy())
+    finally:
+        fn.release()
