@@ -90,6 +90,12 @@ typedef struct {
     sage_dev_alloc_fn dev_alloc;   /* optional */
     sage_dev_free_fn dev_free;     /* optional; set both or neither */
     void* alloc_ctx;
+    size_t host_cache_bytes;       /* stage 2 of the multi-stage exit (Sec. 5.3): when the last
+                                      reference of a key is released, its read-only data is kept in
+                                      page-locked host memory (up to this many bytes, least recently
+                                      used images evicted) and a later prepare of the key re-stages
+                                      from there at link speed instead of calling its producer.
+                                      0 = off (release frees everything). */
 } sage_pool_config;
 
 /* Producer of a data item: fill bytes [offset, offset+bytes) of the item into the
@@ -180,6 +186,10 @@ typedef struct {
     double last_module_ms;         /* kernel loading + attribute setup of the last miss */
     double last_workspace_ms;      /* workspace allocation + tensor-map setup of the last miss */
     double last_prepare_ms;        /* wall time of the last sage_prepare call */
+    size_t host_cache_bytes;       /* read-only images held in the host cache */
+    int64_t host_cache_entries;
+    int64_t host_cache_hits;       /* prepares re-staged from the host cache */
+    int64_t demotions;             /* releases that moved read-only data to the host cache */
 } sage_pool_stats;
 
 /* Create a pool on config->device: makes the CUDA context current, creates the

@@ -28,7 +28,8 @@ class PoolConfig(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
                 ("staging_chunk_bytes", ctypes.c_size_t), ("staging_chunks", ctypes.c_int),
                 ("producer_threads", ctypes.c_int), ("serial_setup", ctypes.c_int),
-                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
+                ("host_cache_bytes", ctypes.c_size_t)]
 
 
 class DataDesc(ctypes.Structure):
@@ -90,7 +91,9 @@ class PoolStats(ctypes.Structure):
                 ("misses", ctypes.c_int64), ("invocations", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("ctx_ms", ctypes.c_double), ("last_stage_ms", ctypes.c_double),
                 ("last_fill_ms", ctypes.c_double), ("last_module_ms", ctypes.c_double),
-                ("last_workspace_ms", ctypes.c_double), ("last_prepare_ms", ctypes.c_double)]
+                ("last_workspace_ms", ctypes.c_double), ("last_prepare_ms", ctypes.c_double),
+                ("host_cache_bytes", ctypes.c_size_t), ("host_cache_entries", ctypes.c_int64),
+                ("host_cache_hits", ctypes.c_int64), ("demotions", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) of every exported entry point of include/sage.h

@@ -111,6 +111,17 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
           o.y = pack_bf16x2(acc[w][2], acc[w][3]);
           o.z = pack_bf16x2(acc[w][4], acc[w][5]);
           o.w = pack_bf16x2(acc[w][6], acc[w][7]);
+        } else if (a.out_lo) {
+          // hi/lo planes for the fp32 tensor-core layers: hi = tf32(sum), lo = sum - hi
+          float h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            h[e] = to_tf32_rna(acc[w][e]);
+            l[e] = acc[w][e] - h[e];
+          }
+          o = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+          float* lrow = a.out_lo + static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim;
+          reinterpret_cast<float4*>(lrow)[col + w * LPR] = make_float4(l[0], l[1], l[2], l[3]);
         } else {
           o = make_uint4(__float_as_uint(acc[w][0]), __float_as_uint(acc[w][1]), __float_as_uint(acc[w][2]),
                          __float_as_uint(acc[w][3]));

@@ -18,6 +18,8 @@
 //   warps 2-5        : epilogue -- tcgen05.ld of 32 TMEM lanes each, bias, ReLU,
 //                      fp32 16-byte stores.
 // Each output's k order is fixed, so a row's result does not depend on M.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace sage {
@@ -185,6 +187,171 @@ __global__ void __launch_bounds__(192, 1)
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// Pre-split operands: X and W arrive as hi/lo planes (x = hi + lo, hi = tf32(x)),
+// so the pipeline is TMA -> MMA only (4 warps: warp 0 lane 0 loads the four
+// tiles of a stage, warp 1 lane 0 issues the MMAs, all four warps run the
+// epilogue).  The epilogue writes the output as hi/lo planes too, ready for the
+// next layer.  Same products in the same order as the splitting kernel above,
+// so the results are bitwise the same.
+template <int BN, int NST>
+__global__ void __launch_bounds__(128, 1)
+    gemm_tf32x3_presplit_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                                const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                                int M, int N, int K, const float* __restrict__ bias, int relu,
+                                float* __restrict__ Yh, float* __restrict__ Yl, int ldy, int* err) {
+  using C = Tf32Cfg<BN, NST>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto a_hi = [&](int s) { return smem + s * C::STAGE; };
+  auto b_hi = [&](int s) { return smem + s * C::STAGE + C::A_BYTES; };
+  auto a_lo = [&](int s) { return smem + s * C::STAGE + C::A_BYTES + C::B_BYTES; };
+  auto b_lo = [&](int s) { return smem + s * C::STAGE + 2 * C::A_BYTES + C::B_BYTES; };
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accum = empty + C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
+  const int KB = (K + kBK - 1) / kBK;
+
+  if (warp == 0) tmem_alloc(tmem_slot, BN);
+  if (warp == 1 && lane == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accum, 1);
+    fence_mbar_init();
+  }
+  if (warp == 2 && lane == 0) {
+    tma_prefetch_desc(&tmAh);
+    tma_prefetch_desc(&tmAl);
+    tma_prefetch_desc(&tmBh);
+    tma_prefetch_desc(&tmBl);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (kb / C::STAGES) & 1;
+      if (!mbar_wait(&empty[s], ph ^ 1, err)) break;
+      mbar_arrive_expect_tx(&full[s], C::STAGE);
+      tma_load_2d(a_hi(s), &tmAh, kb * kBK, m0, &full[s]);
+      tma_load_2d(a_lo(s), &tmAl, kb * kBK, m0, &full[s]);
+      tma_load_2d(b_hi(s), &tmBh, kb * kBK, n0, &full[s]);
+      tma_load_2d(b_lo(s), &tmBl, kb * kBK, n0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_tf32_f32(kBM, BN);
+    for (int kb = 0; kb < KB; ++kb) {
+      const int s = kb % C::STAGES;
+      const uint32_t ph = (kb / C::STAGES) & 1;
+      if (!mbar_wait(&full[s], ph, err)) break;
+      tc_fence_after();
+      const uint32_t ah = smem_u32(a_hi(s)), bh = smem_u32(b_hi(s));
+      const uint32_t al = smem_u32(a_lo(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+      for (int k = 0; k < kBK / 8; ++k) {
+        const uint32_t o = k * 32;
+        tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
+        tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+        tc_mma_tf32(tmem, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
+      }
+      tc_commit(&empty[s]);
+    }
+    tc_commit(accum);
+  }
+  __syncwarp();
+
+  mbar_wait(accum, 0, err);
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+  const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld_32cols(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+    tmem_ld_wait();
+    if (row < M) {
+      float4* dh = reinterpret_cast<float4*>(Yh + ro + c0);
+      float4* dl = reinterpret_cast<float4*>(Yl + ro + c0);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          o[q] = __uint_as_float(v[4 * j + q]) + __ldg(bias + n0 + c0 + 4 * j + q);
+          if (relu) o[q] = fmaxf(o[q], 0.f);
+        }
+        float4 h, l;
+        h.x = to_tf32_rna(o[0]);
+        h.y = to_tf32_rna(o[1]);
+        h.z = to_tf32_rna(o[2]);
+        h.w = to_tf32_rna(o[3]);
+        l.x = o[0] - h.x;
+        l.y = o[1] - h.y;
+        l.z = o[2] - h.z;
+        l.w = o[3] - h.w;
+        dh[j] = h;
+        dl[j] = l;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+__global__ void split_planes_kernel(const float* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo,
+                                    size_t n) {
+  for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const float v = src[i];
+    const float h = to_tf32_rna(v);
+    hi[i] = h;
+    lo[i] = v - h;
+  }
+}
+
+template <int BN, int NST>
+cudaError_t launch_presplit_bn(int M, int N, int K, const float* xh, const float* xl, int ldx, const float* wh,
+                               const float* wl, const float* bias, int relu, float* yh, float* yl, int ldy, int* err,
+                               cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_presplit_kernel<BN, NST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap tah, tal, tbh, tbl;
+  if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
+      !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN))
+    return cudaErrorInvalidValue;
+  dim3 grid(N / BN, (M + kBM - 1) / kBM);
+  gemm_tf32x3_presplit_kernel<BN, NST><<<grid, 128, Tf32Cfg<BN, NST>::SMEM, s>>>(tah, tal, tbh, tbl, M, N, K, bias,
+                                                                                 relu, yh, yl, ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_presplit_cfg(GemmCfg c, int M, int N, int K, const float* xh, const float* xl, int ldx,
+                                const float* wh, const float* wl, const float* bias, int relu, float* yh, float* yl,
+                                int ldy, int* err, cudaStream_t s) {
+  if (c.bn == 128 && c.stages == 3)
+    return launch_presplit_bn<128, 3>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  if (c.bn == 64 && c.stages == 4)
+    return launch_presplit_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  if (c.bn == 64 && c.stages == 2)
+    return launch_presplit_bn<64, 2>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  return cudaErrorInvalidValue;
+}
+
 template <int BN, int NST>
 cudaError_t launch_bn(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias, int relu,
                       float* y, int ldy, int* err, cudaStream_t s) {
@@ -221,6 +388,10 @@ int g_sms = 0;
 
 void preload_tf32_kernels() {
   cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<128, 3>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<64, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<64, 2>);
+  cudaFuncGetAttributes(&fa, split_planes_kernel);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<128, 3>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64, 4>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64, 2>);
@@ -251,6 +422,37 @@ cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, c
   const int mt = (M + kBM - 1) / kBM;
   if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return launch_bn<64, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+}
+
+cudaError_t launch_linear_f32_tc_presplit(int M, int N, int K, const float* xh, const float* xl, int ldx,
+                                          const float* wh, const float* wl, const float* bias, int relu, float* yh,
+                                          float* yl, int ldy, int* err, cudaStream_t s, GemmCfg cfg) {
+  if (M <= 0) return cudaSuccess;
+  if (K <= 0 || (K % 4) || (N % 64) || (ldx % 4) || (ldy % 4)) return cudaErrorInvalidValue;
+  for (const void* p : {static_cast<const void*>(xh), static_cast<const void*>(xl), static_cast<const void*>(wh),
+                        static_cast<const void*>(wl), static_cast<const void*>(yh), static_cast<const void*>(yl)})
+    if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  if (cfg.bn) {
+    if (N % cfg.bn) return cudaErrorInvalidValue;
+    return launch_presplit_cfg(cfg, M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  }
+  const int mt = (M + kBM - 1) / kBM;
+  if (N % 128 == 0 && mt * (N / 128) >= g_sms)
+    return launch_presplit_bn<128, 3>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  return launch_presplit_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+}
+
+cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int blocks = static_cast<int>(std::min<size_t>((n + 255) / 256, 4096));
+  split_planes_kernel<<<blocks, 256, 0, s>>>(src, hi, lo, n);
+  count_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace sage

@@ -31,18 +31,19 @@ struct GatherArgs {
   void* out;                         // [M, ldo] elements of the table dtype
   int ldo;
   int* err;
+  float* out_lo = nullptr;           // fp32 only, optional: out becomes the tf32 hi plane, out_lo the residual
 };
 cudaError_t launch_gather(const GatherArgs& a, const InvTable& tab, cudaStream_t s);
 
 // Bottom layer 0: y = ReLU(dense W0^T + b0) with the dense rows read from each
 // invocation of the batch.  W0 [N, K] in the dtype, y [M, ldy] in the dtype.
 cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const void* W, const float* bias,
-                           void* y, int ldy, cudaStream_t s);
+                           void* y, int ldy, cudaStream_t s, float* y_lo = nullptr);
 
 // Head: out_i[b] = sigmoid(h[r, :] . w + c) for every row r of the batch, written
 // to its invocation's out.  h [M, ldh] in the dtype, w [K] in the dtype, c fp32.
 cudaError_t launch_head(int dtype, const InvTable& tab, int K, const void* h, int ldh, const void* w,
-                        const float* c, cudaStream_t s);
+                        const float* c, cudaStream_t s, const float* h_lo = nullptr);
 
 // 2-D TMA tensor map of a row-major matrix [rows, cols] (row stride ld elements;
 // dtype 0 fp32, 1 bf16), boxes of box_rows x box_cols, 128-byte swizzle, zero
@@ -56,7 +57,7 @@ struct GemmCfg {
   int bn;
   int stages;
 };
-enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2 };
+enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2, kGemmTf32Pre = 3 };
 int gemm_candidates(int kind, GemmCfg* out, int max);
 int tf32_candidates(GemmCfg* out, int max);
 // Tuned configuration for a GEMM shape ({0, 0} if none was tuned).
@@ -70,6 +71,13 @@ cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, cons
 cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, const void* W,
                                   const float* bias, int relu, void* y, int ldy, int* err, cudaStream_t s,
                                   GemmCfg cfg = GemmCfg{0, 0});
+// fp32 layer on the tensor cores from pre-split hi/lo planes of x and W; writes
+// its output as hi/lo planes.
+cudaError_t launch_linear_f32_tc_presplit(int M, int N, int K, const float* xh, const float* xl, int ldx,
+                                          const float* wh, const float* wl, const float* bias, int relu, float* yh,
+                                          float* yl, int ldy, int* err, cudaStream_t s, GemmCfg cfg = GemmCfg{0, 0});
+// hi[i] = tf32(src[i]) (round to nearest), lo[i] = src[i] - hi[i].
+cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s);
 // fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.
 cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
                                  int relu, float* y, int ldy, int* err, cudaStream_t s, GemmCfg cfg = GemmCfg{0, 0});

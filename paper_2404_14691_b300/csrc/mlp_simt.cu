@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256, 2) sgemm_nt_kernel(int M, int N, int K, c
 template <bool BF16>
 __global__ void __launch_bounds__(256) bottom0_kernel(const __grid_constant__ InvTable tab, int K, int N,
                                                       const void* __restrict__ Wv, const float* __restrict__ bias,
-                                                      void* __restrict__ y, int ldy) {
+                                                      void* __restrict__ y, int ldy, float* __restrict__ y_lo) {
   extern __shared__ float sm[];  // [N*K] weights then [N] bias
   float* sW = sm;
   float* sb = sm + static_cast<size_t>(N) * K;
@@ -192,10 +192,15 @@ __global__ void __launch_bounds__(256) bottom0_kernel(const __grid_constant__ In
       }
       if (j >= N) continue;
       s = fmaxf(s + sb[j], 0.f);
+      const size_t o = static_cast<size_t>(r) * ldy + j;
       if (BF16) {
-        reinterpret_cast<__nv_bfloat16*>(y)[static_cast<size_t>(r) * ldy + j] = __float2bfloat16_rn(s);
+        reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(s);
+      } else if (y_lo) {
+        const float h = to_tf32_rna(s);
+        reinterpret_cast<float*>(y)[o] = h;
+        y_lo[o] = s - h;
       } else {
-        reinterpret_cast<float*>(y)[static_cast<size_t>(r) * ldy + j] = s;
+        reinterpret_cast<float*>(y)[o] = s;
       }
     }
   }
@@ -210,7 +215,7 @@ template <bool BF16>
 __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant__ InvTable tab, int K, int N,
                                                            const void* __restrict__ Wv,
                                                            const float* __restrict__ bias, void* __restrict__ y,
-                                                           int ldy) {
+                                                           int ldy, float* __restrict__ y_lo) {
   constexpr int R = 32, KM = 16;
   __shared__ float sx[R][KM];
   __shared__ const float* srow[R];
@@ -254,8 +259,15 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
         if (k < K) s = fmaf(sx[rr][k], w[k], s);
       s = fmaxf(s + bj, 0.f);
       const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
-      if (BF16) reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(s);
-      else reinterpret_cast<float*>(y)[o] = s;
+      if (BF16) {
+        reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(s);
+      } else if (y_lo) {
+        const float h = to_tf32_rna(s);
+        reinterpret_cast<float*>(y)[o] = h;
+        y_lo[o] = s - h;
+      } else {
+        reinterpret_cast<float*>(y)[o] = s;
+      }
     }
   }
 }
@@ -267,7 +279,7 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
 template <bool BF16>
 __global__ void __launch_bounds__(256) head_kernel(const __grid_constant__ InvTable tab, int K,
                                                   const void* __restrict__ h, int ldh, const void* __restrict__ w,
-                                                  const float* __restrict__ c) {
+                                                  const float* __restrict__ c, const float* __restrict__ h_lo) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < tab.M; r += warps) {
@@ -279,7 +291,13 @@ __global__ void __launch_bounds__(256) head_kernel(const __grid_constant__ InvTa
     } else {
       const float* hr = reinterpret_cast<const float*>(h) + static_cast<size_t>(r) * ldh;
       const float* ww = reinterpret_cast<const float*>(w);
-      for (int k = lane; k < K; k += 32) s = fmaf(hr[k], ww[k], s);
+      if (h_lo) {
+        // hi + lo planes: the sum is the fp32 value exactly (lo is the exact residual)
+        const float* lr = h_lo + static_cast<size_t>(r) * ldh;
+        for (int k = lane; k < K; k += 32) s = fmaf(hr[k] + lr[k], ww[k], s);
+      } else {
+        for (int k = lane; k < K; k += 32) s = fmaf(hr[k], ww[k], s);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -333,13 +351,13 @@ cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, cons
 }
 
 cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const void* W, const float* bias,
-                           void* y, int ldy, cudaStream_t s) {
+                           void* y, int ldy, cudaStream_t s, float* y_lo) {
   if (tab.M <= 0) return cudaSuccess;
   if (K < 1 || K > 64) return cudaErrorInvalidValue;
   if (K <= 16) {
     const int blocks = (tab.M + 31) / 32;
-    if (dtype == 1) bottom0_thin_kernel<true><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy);
-    else bottom0_thin_kernel<false><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy);
+    if (dtype == 1) bottom0_thin_kernel<true><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy, nullptr);
+    else bottom0_thin_kernel<false><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy, y_lo);
     count_launch();
     return cudaGetLastError();
   }
@@ -350,25 +368,25 @@ cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const v
   if (blocks > cap) blocks = cap;
   if (dtype == 1) {
     cudaFuncSetAttribute(bottom0_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    bottom0_kernel<true><<<blocks, 256, smem, s>>>(tab, K, N, W, bias, y, ldy);
+    bottom0_kernel<true><<<blocks, 256, smem, s>>>(tab, K, N, W, bias, y, ldy, nullptr);
   } else {
     cudaFuncSetAttribute(bottom0_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    bottom0_kernel<false><<<blocks, 256, smem, s>>>(tab, K, N, W, bias, y, ldy);
+    bottom0_kernel<false><<<blocks, 256, smem, s>>>(tab, K, N, W, bias, y, ldy, y_lo);
   }
   count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_head(int dtype, const InvTable& tab, int K, const void* h, int ldh, const void* w,
-                        const float* c, cudaStream_t s) {
+                        const float* c, cudaStream_t s, const float* h_lo) {
   if (tab.M <= 0) return cudaSuccess;
   int blocks = (tab.M + 7) / 8;
   const int cap = sms() * 8;
   if (blocks > cap) blocks = cap;
   if (dtype == 1) {
-    head_kernel<true><<<blocks, 256, 0, s>>>(tab, K, h, ldh, w, c);
+    head_kernel<true><<<blocks, 256, 0, s>>>(tab, K, h, ldh, w, c, nullptr);
   } else {
-    head_kernel<false><<<blocks, 256, 0, s>>>(tab, K, h, ldh, w, c);
+    head_kernel<false><<<blocks, 256, 0, s>>>(tab, K, h, ldh, w, c, h_lo);
   }
   count_launch();
   return cudaGetLastError();

@@ -202,6 +202,17 @@ struct Slot {
 
 struct sage_pool_s;
 
+// Read-only data of one key kept in page-locked host memory (stage 2 of the
+// multi-stage exit): the tables and weights items exactly as on the device.
+struct HostImage {
+  char* tables = nullptr;
+  char* weights = nullptr;
+  size_t tb = 0, wb = 0;
+  std::string sig;     // shape signature the image belongs to
+  uint64_t last = 0;   // LRU clock
+  size_t bytes() const { return tb + wb; }
+};
+
 struct Entry {
   sage_pool_s* pool = nullptr;
   std::string key;
@@ -215,6 +226,15 @@ struct Entry {
   std::vector<Layer> layers;
   int64_t table_off[kMaxTables] = {};
   int refs = 0;
+  std::string sig;        // shape signature (dtype, tables, layers, item sizes)
+  // fp32 functions whose hidden layers all tile on the tensor cores keep every
+  // activation as two planes (tf32 hi, fp32 residual lo) and the hidden-layer
+  // weights split the same way (computed once after staging)
+  bool presplit = false;
+  char* d_wsplit = nullptr;
+  size_t wsplit_bytes = 0;
+  std::vector<std::pair<const float*, const float*>> wplanes;  // per layer: (hi, lo) or nulls
+  HostImage owned;        // host image this entry was re-staged from (kept for the next demotion)
 
   // staging (the read-only data's journey host -> device)
   sage_data_desc tdesc{}, wdesc{};
@@ -269,6 +289,10 @@ struct sage_pool_s {
   std::mutex mu;
   std::unordered_map<std::string, Entry*> entries;
   std::unordered_set<sage_fn_s*> handles;
+  // stage-2 host cache of released keys' read-only data
+  size_t host_budget = 0, host_used = 0;
+  std::unordered_map<std::string, HostImage> hcache;
+  uint64_t hclock = 0;
   sage_pool_stats st{};
   std::atomic<int64_t> h2d{0}, invocations{0};
 
@@ -300,6 +324,37 @@ bool is_pinned(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeHost;
+}
+
+std::string shape_sig(const sage_fn_desc* d) {
+  std::string s = std::to_string(d->dtype) + "|" + std::to_string(d->num_tables) + "|" + std::to_string(d->dim) +
+                  "|" + std::to_string(d->n_dense) + "|";
+  for (int t = 0; t < d->num_tables; ++t) s += std::to_string(d->rows[t]) + ",";
+  s += "|";
+  for (int l = 0; l < d->n_bot; ++l) s += std::to_string(d->bot_dims[l]) + ",";
+  s += "|";
+  for (int l = 0; l < d->n_top; ++l) s += std::to_string(d->top_dims[l]) + ",";
+  return s + "|" + std::to_string(d->tables.bytes) + "|" + std::to_string(d->weights.bytes);
+}
+
+void free_image(sage_pool_s* P, HostImage& h) {
+  if (h.tables) host_free_pinned(h.tables);
+  if (h.weights) host_free_pinned(h.weights);
+  P->host_used -= std::min(P->host_used, h.bytes());
+  h = HostImage();
+}
+
+// Make room for `need` bytes of host images (P->mu held); false if impossible.
+bool host_cache_make_room(sage_pool_s* P, size_t need) {
+  if (need > P->host_budget) return false;
+  while (P->host_used + need > P->host_budget && !P->hcache.empty()) {
+    auto victim = P->hcache.begin();
+    for (auto it = P->hcache.begin(); it != P->hcache.end(); ++it)
+      if (it->second.last < victim->second.last) victim = it;
+    free_image(P, victim->second);
+    P->hcache.erase(victim);
+  }
+  return P->host_used + need <= P->host_budget;
 }
 
 // Stage one data item into dst: fill pinned ring chunks on the host workers and
@@ -350,6 +405,16 @@ void stage_entry(sage_pool_s* P, Entry* e) {
   double fill_ms = 0;
   bool ok = stage_item(P, e, e->wdesc, e->d_weights, &fill_ms) &&
             stage_item(P, e, e->tdesc, e->d_tables, &fill_ms);
+  if (ok && e->presplit) {
+    for (size_t l = 0; l < e->wplanes.size(); ++l) {
+      if (!e->wplanes[l].first) continue;
+      const Layer& L = e->layers[l];
+      if (launch_split_planes(static_cast<const float*>(L.W), const_cast<float*>(e->wplanes[l].first),
+                              const_cast<float*>(e->wplanes[l].second), static_cast<size_t>(L.in) * L.out,
+                              P->side) != cudaSuccess)
+        ok = false;
+    }
+  }
   // the ready event covers every copy queued for this entry, also on failure
   if (cudaEventRecord(e->ready, P->side) != cudaSuccess) ok = false;
   const double stage_ms = ms_since(e->t_prepare);
@@ -441,11 +506,17 @@ double load_kernels_once() {
   return spent;
 }
 
+// planes per activation buffer: 2 (hi, lo) for pre-split fp32 functions
+size_t planes(const Entry* e) { return e->presplit ? 2 : 1; }
+
 size_t slot_bytes(const Entry* e, int cap) {
   size_t b = 0;
-  for (size_t l = 0; l + 1 < e->bot.size(); ++l) b += align256(static_cast<size_t>(cap) * e->bot[l] * e->elem());
-  b += align256(static_cast<size_t>(cap) * e->concat_dim() * e->elem());
-  for (size_t l = 0; l + 1 < e->top.size(); ++l) b += align256(static_cast<size_t>(cap) * e->top[l] * e->elem());
+  const size_t pl = planes(e);
+  for (size_t l = 0; l + 1 < e->bot.size(); ++l)
+    b += align256(pl * static_cast<size_t>(cap) * e->bot[l] * e->elem());
+  b += align256(pl * static_cast<size_t>(cap) * e->concat_dim() * e->elem());
+  for (size_t l = 0; l + 1 < e->top.size(); ++l)
+    b += align256(pl * static_cast<size_t>(cap) * e->top[l] * e->elem());
   return b;
 }
 
@@ -461,15 +532,16 @@ sage_status build_slot(Entry* e, Slot& s, int cap, cudaStream_t stream) {
   s.bot.clear();
   s.top.clear();
   size_t o = 0;
+  const size_t pl = planes(e);
   for (size_t l = 0; l + 1 < e->bot.size(); ++l) {
     s.bot.push_back(buf + o);
-    o += align256(static_cast<size_t>(cap) * e->bot[l] * e->elem());
+    o += align256(pl * static_cast<size_t>(cap) * e->bot[l] * e->elem());
   }
   s.concat = buf + o;
-  o += align256(static_cast<size_t>(cap) * e->concat_dim() * e->elem());
+  o += align256(pl * static_cast<size_t>(cap) * e->concat_dim() * e->elem());
   for (size_t l = 0; l + 1 < e->top.size(); ++l) {
     s.top.push_back(buf + o);
-    o += align256(static_cast<size_t>(cap) * e->top[l] * e->elem());
+    o += align256(pl * static_cast<size_t>(cap) * e->top[l] * e->elem());
   }
   return SAGE_OK;
 }
@@ -568,6 +640,55 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
     }
     if (s.copied) cudaEventDestroy(s.copied);
   }
+  // stage 2 of the multi-stage exit: keep the read-only data in the host cache
+  bool ok_data = false;
+  {
+    std::lock_guard<std::mutex> g(e->smu);
+    ok_data = e->sstate == 1 && e->setup == 1;
+  }
+  if (P->host_budget > 0 && ok_data) {
+    std::unique_lock<std::mutex> g(P->mu);
+    HostImage img = e->owned;
+    e->owned = HostImage();
+    bool have = img.tables != nullptr;
+    if (!have && host_cache_make_room(P, e->tables_bytes + e->weights_bytes)) {
+      cudaError_t he = cudaSuccess;
+      img.tables = static_cast<char*>(host_alloc_pinned(e->tables_bytes, &he));
+      img.weights = static_cast<char*>(host_alloc_pinned(e->weights_bytes, &he));
+      img.tb = e->tables_bytes;
+      img.wb = e->weights_bytes;
+      if (img.tables && img.weights) {
+        P->host_used += img.bytes();
+        g.unlock();
+        bool copied = cudaMemcpyAsync(img.tables, e->d_tables, img.tb, cudaMemcpyDeviceToHost, P->alloc) ==
+                          cudaSuccess &&
+                      cudaMemcpyAsync(img.weights, e->d_weights, img.wb, cudaMemcpyDeviceToHost, P->alloc) ==
+                          cudaSuccess &&
+                      cudaStreamSynchronize(P->alloc) == cudaSuccess;
+        g.lock();
+        have = copied;
+        if (!copied) free_image(P, img);
+      } else {
+        if (img.tables) host_free_pinned(img.tables);
+        if (img.weights) host_free_pinned(img.weights);
+        img = HostImage();
+      }
+    }
+    if (have) {
+      img.sig = e->sig;
+      img.last = ++P->hclock;
+      auto old = P->hcache.find(e->key);
+      if (old != P->hcache.end()) {
+        free_image(P, old->second);
+        P->hcache.erase(old);
+      }
+      P->hcache[e->key] = img;
+      P->st.demotions++;
+    }
+  } else if (e->owned.tables) {
+    std::lock_guard<std::mutex> g(P->mu);
+    free_image(P, e->owned);
+  }
   // every use of the entry's memory has finished (ready + slot events above)
   for (auto& s : e->slots) {
     P->dev_free(s.buf, s.bytes, P->alloc);
@@ -575,6 +696,7 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
   }
   P->dev_free(e->d_tables, e->tables_bytes, P->alloc);
   P->dev_free(e->d_weights, e->weights_bytes, P->alloc);
+  P->dev_free(e->d_wsplit, e->wsplit_bytes, P->alloc);
   P->dev_free(e->d_err, 256, P->alloc);
   cudaStreamSynchronize(P->alloc);
   if (e->ready) cudaEventDestroy(e->ready);
@@ -617,6 +739,17 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   const size_t es = e->elem();
   const int cd = e->concat_dim();
   char* bot_out = s.concat + static_cast<size_t>(e->T) * e->dim * es;
+  // pre-split fp32: the lo plane of a buffer with row stride ld sits cap*ld floats after its hi plane
+  const bool ps2 = e->presplit;
+  auto lo_of = [&](const void* hi, int ld) -> float* {
+    return ps2 ? const_cast<float*>(static_cast<const float*>(hi)) + static_cast<size_t>(s.cap) * ld : nullptr;
+  };
+  auto f32_presplit = [&](const Layer& L, int l, const void* x, int ldx, void* y, int ldy) -> cudaError_t {
+    return launch_linear_f32_tc_presplit(M, L.out, L.in, static_cast<const float*>(x), lo_of(x, ldx), ldx,
+                                         e->wplanes[l].first, e->wplanes[l].second, L.b, 1,
+                                         static_cast<float*>(y), lo_of(y, ldy), ldy, e->d_err, stream,
+                                         tuned_gemm(kGemmTf32Pre, M, L.out, L.in));
+  };
   // fork: the bottom MLP (columns [T*dim, cd) of the concat buffer) runs on the
   // slot's branch stream while the gather (columns [0, T*dim)) runs on `stream`
   // (while kernel timing is on, the branch is serialised so that each kernel's
@@ -632,7 +765,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     void* y = nb == 1 ? bot_out : s.bot[0];
     const int ldy = nb == 1 ? cd : e->bot[0];
     ProfScope ps(stream, kProfBottom0, 2.0 * M * L0.in * L0.out);
-    SAGE_CK(launch_bottom0(e->dtype, tab, L0.in, L0.out, L0.W, L0.b, y, ldy, stream));
+    SAGE_CK(launch_bottom0(e->dtype, tab, L0.in, L0.out, L0.W, L0.b, y, ldy, stream, lo_of(y, ldy)));
   }
   for (int l = 1; l < nb; ++l) {
     const Layer& L = e->layers[l];
@@ -644,6 +777,8 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     if (e->dtype == SAGE_BF16)
       SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, L.in, L.W, L.b, 1, y, ldy, e->d_err, stream,
                                     tuned_gemm(kGemmBf16, M, L.out, L.in)));
+    else if (ps2)
+      SAGE_CK(f32_presplit(L, l, x, L.in, y, ldy));
     else
       SAGE_CK(launch_f32_layer(M, L.out, L.in, static_cast<const float*>(x), L.in, static_cast<const float*>(L.W),
                                L.b, 1, static_cast<float*>(y), ldy, e->d_err, stream));
@@ -664,6 +799,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     a.out = s.concat;
     a.ldo = cd;
     a.err = e->d_err;
+    a.out_lo = lo_of(s.concat, cd);
     // algorithmic bytes: each lookup reads a row and its index, each bag reads its
     // offset and writes one pooled row
     double lookups = 0;
@@ -685,6 +821,8 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     if (e->dtype == SAGE_BF16)
       SAGE_CK(launch_linear_bf16_tc(M, L.out, L.in, x, ldx, L.W, L.b, 1, y, L.out, e->d_err, stream,
                                     tuned_gemm(kGemmBf16, M, L.out, L.in)));
+    else if (ps2)
+      SAGE_CK(f32_presplit(L, nb + l, x, ldx, y, L.out));
     else
       SAGE_CK(launch_f32_layer(M, L.out, L.in, reinterpret_cast<const float*>(x), ldx,
                                static_cast<const float*>(L.W), L.b, 1, reinterpret_cast<float*>(y), L.out,
@@ -695,7 +833,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   // sigmoid head, written to each invocation's out
   const Layer& H = e->layers[nb + nt - 1];
   ProfScope ps(stream, kProfHead, 2.0 * M * H.in);
-  SAGE_CK(launch_head(e->dtype, tab, H.in, x, ldx, H.W, H.b, stream));
+  SAGE_CK(launch_head(e->dtype, tab, H.in, x, ldx, H.W, H.b, stream, lo_of(x, ldx)));
   return SAGE_OK;
 }
 
@@ -815,6 +953,7 @@ sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
   P->dfree = c.dev_free;
   P->actx = c.alloc_ctx;
   P->serial_setup = c.serial_setup != 0;
+  P->host_budget = c.host_cache_bytes;
   size_t free_b = 0, total_b = 0;
   SAGE_CK(cudaMemGetInfo(&free_b, &total_b));
   const size_t margin = size_t(2) << 30;
@@ -885,11 +1024,41 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     e->weights_bytes = d->weights.bytes;
     e->tdesc = d->tables;
     e->wdesc = d->weights;
+    e->sig = shape_sig(d);
+    {
+      auto hc = P->hcache.find(e->key);
+      if (hc != P->hcache.end() && hc->second.sig == e->sig) {
+        // re-stage from the host image (stage 2 -> resident): no producer call
+        e->owned = hc->second;
+        P->hcache.erase(hc);
+        e->tdesc.host_src = e->owned.tables;
+        e->tdesc.fill = nullptr;
+        e->wdesc.host_src = e->owned.weights;
+        e->wdesc.fill = nullptr;
+        P->st.host_cache_hits++;
+      }
+    }
     e->max_batch = d->max_batch > 0 ? d->max_batch : 4096;
+    if (e->dtype == SAGE_F32) {
+      // pre-split planes when every hidden layer runs on the tensor cores
+      std::vector<std::pair<int, int>> dims;
+      int prev = e->n_dense;
+      for (int v : e->bot) dims.push_back({prev, v}), prev = v;
+      prev = e->concat_dim();
+      for (int v : e->top) dims.push_back({prev, v}), prev = v;
+      bool all = dims.size() > 2;
+      for (size_t l = 1; l + 1 < dims.size(); ++l)
+        all = all && f32_on_tensor_cores(dims[l].second, dims[l].first, dims[l].first, dims[l].second) &&
+              (e->concat_dim() % 4) == 0;
+      e->presplit = all;
+      if (all)
+        for (size_t l = 1; l + 1 < dims.size(); ++l)
+          e->wsplit_bytes += 2 * align256(static_cast<size_t>(dims[l].first) * dims[l].second * 4);
+    }
     const int nslots = d->workspace_slots > 0 ? d->workspace_slots : 2;
     e->slots.resize(nslots);
     e->ws_bytes = static_cast<size_t>(nslots) * slot_bytes(e, e->max_batch);
-    const size_t need = align256(e->tables_bytes) + align256(e->weights_bytes) + e->ws_bytes + 256;
+    const size_t need = align256(e->tables_bytes) + align256(e->weights_bytes) + e->ws_bytes + e->wsplit_bytes + 256;
     if (P->used + need > P->budget) {
       delete e;
       return fail(SAGE_ERR_NOMEM, "prepare of '%s' needs %zu bytes; %zu of %zu in use", d->fn_key, need, P->used,
@@ -932,6 +1101,43 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
   e->d_weights = static_cast<char*>(P->dev_alloc(e->weights_bytes, P->alloc));
   if (!e->d_tables || !e->d_weights)
     return setup_failed(fail(SAGE_ERR_NOMEM, "device allocation of the read-only data of '%s' failed", d->fn_key));
+  if (e->wsplit_bytes) {
+    e->d_wsplit = static_cast<char*>(P->dev_alloc(e->wsplit_bytes, P->alloc));
+    if (!e->d_wsplit) return setup_failed(fail(SAGE_ERR_NOMEM, "split-weight allocation failed"));
+  }
+  {
+    // layer pointers inside the weights item (and the split planes of the hidden layers)
+    size_t o = 0, ow = 0;
+    int prev = e->n_dense;
+    std::vector<std::pair<int, int>> L;
+    for (int v : e->bot) {
+      L.push_back({prev, v});
+      prev = v;
+    }
+    prev = e->concat_dim();
+    for (int v : e->top) {
+      L.push_back({prev, v});
+      prev = v;
+    }
+    for (size_t l = 0; l < L.size(); ++l) {
+      const auto& p = L[l];
+      o = align256(o);
+      const void* W = e->d_weights + o;
+      o += static_cast<size_t>(p.first) * p.second * e->elem();
+      o = align256(o);
+      const float* b = reinterpret_cast<const float*>(e->d_weights + o);
+      o += static_cast<size_t>(p.second) * 4;
+      e->layers.push_back({p.first, p.second, W, b});
+      if (e->presplit && l >= 1 && l + 1 < L.size()) {
+        const size_t pb = align256(static_cast<size_t>(p.first) * p.second * 4);
+        e->wplanes.push_back({reinterpret_cast<const float*>(e->d_wsplit + ow),
+                              reinterpret_cast<const float*>(e->d_wsplit + ow + pb)});
+        ow += 2 * pb;
+      } else {
+        e->wplanes.push_back({nullptr, nullptr});
+      }
+    }
+  }
   // the staging copies (side stream) may target the slab only once it exists
   ce = cudaStreamSynchronize(P->alloc);
   if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "allocation: %s", cudaGetErrorString(ce)));
@@ -963,30 +1169,6 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
   load_kernels_once();
   const double module_ms = ms_since(tm);
   auto tw = Clock::now();
-  {
-    // layer pointers inside the weights item
-    size_t o = 0;
-    int prev = e->n_dense;
-    std::vector<std::pair<int, int>> L;
-    for (int v : e->bot) {
-      L.push_back({prev, v});
-      prev = v;
-    }
-    prev = e->concat_dim();
-    for (int v : e->top) {
-      L.push_back({prev, v});
-      prev = v;
-    }
-    for (auto& p : L) {
-      o = align256(o);
-      const void* W = e->d_weights + o;
-      o += static_cast<size_t>(p.first) * p.second * e->elem();
-      o = align256(o);
-      const float* b = reinterpret_cast<const float*>(e->d_weights + o);
-      o += static_cast<size_t>(p.second) * 4;
-      e->layers.push_back({p.first, p.second, W, b});
-    }
-  }
   e->d_err = static_cast<int*>(P->dev_alloc(256, P->alloc));
   if (!e->d_err) return setup_failed(fail(SAGE_ERR_NOMEM, "error word allocation failed"));
   ce = cudaMemsetAsync(e->d_err, 0, 256, P->alloc);
@@ -1275,7 +1457,8 @@ sage_status sage_autotune(sage_fn f, int rows, void* stream) {
     } else {
       const int ldx = l < nb ? L.in : (l == nb ? e->concat_dim() : L.in);
       const int ldy = l == nb - 1 ? e->concat_dim() : L.out;
-      if (f32_on_tensor_cores(L.out, L.in, ldx, ldy)) kind = kGemmTf32x3;
+      if (e->presplit) kind = kGemmTf32Pre;
+      else if (f32_on_tensor_cores(L.out, L.in, ldx, ldy)) kind = kGemmTf32x3;
     }
     if (!kind) continue;
     sage_status st = autotune_gemm(kind, rows, L.out, L.in, s, nullptr, nullptr);
@@ -1342,6 +1525,8 @@ sage_status sage_pool_destroy(sage_pool P) {
   cudaSetDevice(P->device);
   cudaStreamSynchronize(P->side);
   cudaStreamSynchronize(P->alloc);
+  for (auto& kv : P->hcache) free_image(P, kv.second);
+  P->hcache.clear();
   for (size_t i = 0; i < P->ring.size(); ++i) {
     cudaEventDestroy(P->ring_ev[i]);
   }
@@ -1363,6 +1548,9 @@ sage_status sage_pool_stats_get(sage_pool P, sage_pool_stats* out) {
   s.functions = static_cast<int64_t>(P->entries.size());
   s.refs = static_cast<int64_t>(P->handles.size());
   for (auto& kv : P->entries) s.readonly_bytes += kv.second->tables_bytes + kv.second->weights_bytes;
+  s.host_cache_bytes = 0;
+  for (auto& kv : P->hcache) s.host_cache_bytes += kv.second.bytes();
+  s.host_cache_entries = static_cast<int64_t>(P->hcache.size());
   s.h2d_bytes = P->h2d.load();
   s.invocations = P->invocations.load();
   s.launches = sage::launches();

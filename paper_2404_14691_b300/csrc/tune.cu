@@ -87,10 +87,14 @@ sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg
   for (int c = 0; c < nc; ++c) {
     if (N % cands[c].bn) continue;
     auto run = [&] {
-      return kind == kGemmBf16
-                 ? launch_linear_bf16_tc(Mb, N, K, x, K, w, static_cast<float*>(b), 1, y, N, err, s, cands[c])
-                 : launch_linear_f32_tc(Mb, N, K, static_cast<float*>(x), K, static_cast<float*>(w),
-                                        static_cast<float*>(b), 1, static_cast<float*>(y), N, err, s, cands[c]);
+      if (kind == kGemmBf16)
+        return launch_linear_bf16_tc(Mb, N, K, x, K, w, static_cast<float*>(b), 1, y, N, err, s, cands[c]);
+      if (kind == kGemmTf32Pre)  // the same buffer serves as both planes: timing only
+        return launch_linear_f32_tc_presplit(Mb, N, K, static_cast<float*>(x), static_cast<float*>(x), K,
+                                             static_cast<float*>(w), static_cast<float*>(w), static_cast<float*>(b),
+                                             1, static_cast<float*>(y), static_cast<float*>(y), N, err, s, cands[c]);
+      return launch_linear_f32_tc(Mb, N, K, static_cast<float*>(x), K, static_cast<float*>(w),
+                                  static_cast<float*>(b), 1, static_cast<float*>(y), N, err, s, cands[c]);
     };
     if (run() != cudaSuccess) {
       cudaGetLastError();

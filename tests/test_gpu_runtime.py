@@ -350,3 +350,48 @@ def test_host_allocator_buffers_serve_host_invocations(pool):
         assert np.array_equal(out, d.out.cpu().numpy())
     finally:
         fn.release()
+
+
+def test_multistage_exit_restages_from_the_host_cache():
+    """Stage 2 of the multi-stage exit: released read-only data waits in host memory and a
+    later prepare re-stages it from there without calling the producer."""
+    torch = _torch()
+    p = sage.Pool(device=0, host_cache_bytes=1 << 30)
+    try:
+        spec = spec_small("bf16", key="rt_stage2")
+        inv = workload.make_invocation(spec, 120, seed=31)
+        f = prepare(p, spec)
+        d1 = DevInvocation(inv)
+        f.invoke(*d1.args())
+        torch.cuda.synchronize()
+        f.release()
+        st = p.stats()
+        assert st["demotions"] == 1 and st["host_cache_entries"] == 1 and st["functions"] == 0
+        assert st["host_cache_bytes"] == spec.table_bytes() + workload.weights_blob(spec).nbytes
+        # a producer that fails on its first call proves the data came from the host cache
+        f2 = prepare(p, spec, fail_at_call=1)
+        f2.wait()
+        d2 = DevInvocation(inv)
+        f2.invoke(*d2.args())
+        torch.cuda.synchronize()
+        assert torch.equal(d1.out, d2.out)
+        st = p.stats()
+        assert st["host_cache_hits"] == 1 and st["host_cache_entries"] == 0
+        f2.release()
+        st = p.stats()
+        assert st["demotions"] == 2 and st["host_cache_entries"] == 1
+    finally:
+        p.destroy()
+
+
+def test_host_cache_respects_its_budget():
+    p = sage.Pool(device=0, host_cache_bytes=1 << 20)     # smaller than the function's data
+    try:
+        spec = spec_small("bf16", key="rt_stage2_small")
+        f = prepare(p, spec)
+        f.wait()
+        f.release()
+        st = p.stats()
+        assert st["demotions"] == 0 and st["host_cache_entries"] == 0
+    finally:
+        p.destroy()
