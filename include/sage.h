@@ -301,6 +301,11 @@ int sage_profile_read(sage_kernel_time* out, int max);
  * shape uses.  Synchronous.  sage_tuning_save / _load write / read the table as
  * text keyed by the GPU's name (entries for other GPUs are ignored on load). */
 sage_status sage_autotune(sage_fn fn, int rows, void* stream);
+/* Pin a tile configuration for GEMM shape (kind, batch rows bucket, N, K): kind 1 =
+ * BF16, 2 = fp32 splitting in shared memory, 3 = fp32 from pre-split planes (the
+ * fp32 functions' path; stages >= 100 selects the persistent kernel with stages-100
+ * pipeline stages).  SAGE_ERR_INVALID for configurations the kernel does not have. */
+sage_status sage_tuning_set(int kind, int rows, int N, int K, int bn, int stages);
 sage_status sage_tuning_save(const char* path);
 sage_status sage_tuning_load(const char* path);
 

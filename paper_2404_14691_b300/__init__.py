@@ -235,6 +235,11 @@ class Pool:
             self.handle = None
 
 
+def tuning_set(kind: int, rows: int, N: int, K: int, bn: int, stages: int) -> None:
+    """Pin a tensor-core tile configuration for a GEMM shape (see sage_tuning_set)."""
+    check(lib().sage_tuning_set(kind, rows, N, K, bn, stages), "sage_tuning_set")
+
+
 def tuning_save(path: str) -> None:
     check(lib().sage_tuning_save(path.encode()), "sage_tuning_save")
 

@@ -119,6 +119,7 @@ SIGNATURES = [
     ("sage_profile_enable", _i, [_i]),
     ("sage_profile_read", _i, [ctypes.POINTER(KernelTime), _i]),
     ("sage_autotune", _i, [_vp, _i, _vp]),
+    ("sage_tuning_set", _i, [_i, _i, _i, _i, _i, _i]),
     ("sage_tuning_save", _i, [ctypes.c_char_p]),
     ("sage_tuning_load", _i, [ctypes.c_char_p]),
     ("sage_serve", _i, [_vp, ctypes.POINTER(FnDesc), _i, ctypes.POINTER(Request), _i, ctypes.POINTER(ServeConfig),

@@ -222,6 +222,8 @@ int gemm_candidates(int kind, GemmCfg* out, int max) {
   if (kind == kGemmBf16) {
     for (const GemmCfg& c : kBf16Cfgs)
       if (n < max) out[n++] = c;
+  } else if (kind == kGemmTf32Pre) {
+    n = tf32_presplit_candidates(out, max);
   } else {
     n = tf32_candidates(out, max);
   }

@@ -307,6 +307,165 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// Persistent form of the pre-split kernel: one CTA per SM walks the output tiles
+// (n fastest, so neighbouring CTAs share X tiles in L2).  Two TMEM accumulators
+// alternate between tiles, so the epilogue warps drain tile i while the MMA warp
+// computes tile i+1; the shared-memory ring runs on across tile boundaries.
+//   warp 0 lane 0: TMA producer; warp 1 lane 0: MMA issuer;
+//   warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+template <int BN, int NST>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tf32x3_persistent_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                                  int M, int N, int K, const float* __restrict__ bias, int relu,
+                                  float* __restrict__ Yh, float* __restrict__ Yl, int ldy, int* err) {
+  using C = Tf32Cfg<BN, NST>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  auto a_hi = [&](int s) { return smem + s * C::STAGE; };
+  auto b_hi = [&](int s) { return smem + s * C::STAGE + C::A_BYTES; };
+  auto a_lo = [&](int s) { return smem + s * C::STAGE + C::A_BYTES + C::B_BYTES; };
+  auto b_lo = [&](int s) { return smem + s * C::STAGE + 2 * C::A_BYTES + C::B_BYTES; };
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;  // [2]
+  uint64_t* acc_empty = acc_full + 2;      // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KB = (K + kBK - 1) / kBK;
+  const int NT = N / BN, MT = (M + kBM - 1) / kBM;
+  const int tiles = NT * MT;
+
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * BN);
+  if (warp == 1 && lane == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 2 && lane == 0) {
+    tma_prefetch_desc(&tmAh);
+    tma_prefetch_desc(&tmAl);
+    tma_prefetch_desc(&tmBh);
+    tma_prefetch_desc(&tmBl);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;  // stage use counter across tiles
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % C::STAGES;
+          const uint32_t ph = (g / C::STAGES) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], C::STAGE);
+          tma_load_2d(a_hi(s), &tmAh, kb * kBK, m0, &full[s]);
+          tma_load_2d(a_lo(s), &tmAl, kb * kBK, m0, &full[s]);
+          tma_load_2d(b_hi(s), &tmBh, kb * kBK, n0, &full[s]);
+          tma_load_2d(b_lo(s), &tmBl, kb * kBK, n0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32_f32(kBM, BN);
+      uint32_t g = 0;
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        const int buf = i & 1;
+        const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
+        if (!mbar_wait(&acc_empty[buf], ((i >> 1) & 1) ^ 1, err)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % C::STAGES;
+          const uint32_t ph = (g / C::STAGES) & 1;
+          if (!mbar_wait(&full[s], ph, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(a_hi(s)), bh = smem_u32(b_hi(s));
+          const uint32_t al = smem_u32(a_lo(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+          for (int k = 0; k < kBK / 8; ++k) {
+            const uint32_t o = k * 32;
+            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
+            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+            tc_mma_tf32(acc, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
+          }
+          tc_commit(&empty[s]);
+        }
+        tc_commit(&acc_full[buf]);
+      }
+    }
+  } else {
+    // ---- epilogue warps
+    const int q = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
+      tc_fence_after();
+      const int row = m0 + q * 32 + lane;
+      const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        tmem_ld_wait();
+        if (row < M) {
+          float4* dh = reinterpret_cast<float4*>(Yh + ro + c0);
+          float4* dl = reinterpret_cast<float4*>(Yl + ro + c0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              o[u] = __uint_as_float(v[4 * j + u]) + __ldg(bias + n0 + c0 + 4 * j + u);
+              if (relu) o[u] = fmaxf(o[u], 0.f);
+            }
+            float4 h, l;
+            h.x = to_tf32_rna(o[0]);
+            h.y = to_tf32_rna(o[1]);
+            h.z = to_tf32_rna(o[2]);
+            h.w = to_tf32_rna(o[3]);
+            l.x = o[0] - h.x;
+            l.y = o[1] - h.y;
+            l.z = o[2] - h.z;
+            l.w = o[3] - h.w;
+            dh[j] = h;
+            dl[j] = l;
+          }
+        }
+      }
+      // this thread's TMEM reads of `buf` are complete: hand the buffer back to the MMA warp
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
 __global__ void split_planes_kernel(const float* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo,
                                     size_t n) {
   for (size_t i = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; i < n;
@@ -340,6 +499,36 @@ cudaError_t launch_presplit_bn(int M, int N, int K, const float* xh, const float
   return cudaGetLastError();
 }
 
+int g_sms_p = 0;
+
+template <int BN, int NST>
+cudaError_t launch_persistent_bn(int M, int N, int K, const float* xh, const float* xl, int ldx, const float* wh,
+                                 const float* wl, const float* bias, int relu, float* yh, float* yl, int ldy,
+                                 int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_persistent_kernel<BN, NST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (!g_sms_p) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_p, cudaDevAttrMultiProcessorCount, dev);
+  }
+  CUtensorMap tah, tal, tbh, tbl;
+  if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
+      !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN))
+    return cudaErrorInvalidValue;
+  const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
+  const int grid = tiles < g_sms_p ? tiles : g_sms_p;
+  gemm_tf32x3_persistent_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(tah, tal, tbh, tbl, M, N, K,
+                                                                                   bias, relu, yh, yl, ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_presplit_cfg(GemmCfg c, int M, int N, int K, const float* xh, const float* xl, int ldx,
                                 const float* wh, const float* wl, const float* bias, int relu, float* yh, float* yl,
                                 int ldy, int* err, cudaStream_t s) {
@@ -349,6 +538,11 @@ cudaError_t launch_presplit_cfg(GemmCfg c, int M, int N, int K, const float* xh,
     return launch_presplit_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
   if (c.bn == 64 && c.stages == 2)
     return launch_presplit_bn<64, 2>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  // persistent configurations: stages + 100
+  if (c.bn == 128 && c.stages == 103)
+    return launch_persistent_bn<128, 3>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+  if (c.bn == 64 && c.stages == 104)
+    return launch_persistent_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
   return cudaErrorInvalidValue;
 }
 
@@ -373,6 +567,8 @@ cudaError_t launch_bn(int M, int N, int K, const float* x, int ldx, const float*
 
 // (BN, stages): deep pipelines at 1 CTA per SM, shallow ones at 2 CTAs per SM.
 const GemmCfg kTf32Cfgs[] = {{128, 3}, {64, 4}, {64, 2}};
+// pre-split kernel: the above plus the persistent forms (stages + 100)
+const GemmCfg kTf32PreCfgs[] = {{128, 3}, {64, 4}, {64, 2}, {128, 103}, {64, 104}};
 
 cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
                        int relu, float* y, int ldy, int* err, cudaStream_t s) {
@@ -391,6 +587,8 @@ void preload_tf32_kernels() {
   cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<128, 3>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<64, 4>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<64, 2>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_persistent_kernel<128, 3>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_persistent_kernel<64, 4>);
   cudaFuncGetAttributes(&fa, split_planes_kernel);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<128, 3>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64, 4>);
@@ -400,6 +598,13 @@ void preload_tf32_kernels() {
 int tf32_candidates(GemmCfg* out, int max) {
   int n = 0;
   for (const GemmCfg& c : kTf32Cfgs)
+    if (n < max) out[n++] = c;
+  return n;
+}
+
+int tf32_presplit_candidates(GemmCfg* out, int max) {
+  int n = 0;
+  for (const GemmCfg& c : kTf32PreCfgs)
     if (n < max) out[n++] = c;
   return n;
 }

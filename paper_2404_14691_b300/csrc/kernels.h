@@ -60,6 +60,7 @@ struct GemmCfg {
 enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2, kGemmTf32Pre = 3 };
 int gemm_candidates(int kind, GemmCfg* out, int max);
 int tf32_candidates(GemmCfg* out, int max);
+int tf32_presplit_candidates(GemmCfg* out, int max);
 // Tuned configuration for a GEMM shape ({0, 0} if none was tuned).
 GemmCfg tuned_gemm(int kind, int M, int N, int K);
 // Times every configuration of one shape and records the fastest.

@@ -135,6 +135,18 @@ sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg
 
 }  // namespace sage
 
+extern "C" sage_status sage_tuning_set(int kind, int rows, int N, int K, int bn, int stages) {
+  sage::GemmCfg cands[16];
+  const int nc = sage::gemm_candidates(kind, cands, 16);
+  bool known = false;
+  for (int c = 0; c < nc; ++c) known |= cands[c].bn == bn && cands[c].stages == stages;
+  if (!known || rows < 1 || N < 1 || K < 1 || (N % bn))
+    return sage::set_last_error("unknown tile configuration for this GEMM kind or shape"), SAGE_ERR_INVALID;
+  std::lock_guard<std::mutex> g(sage::g_mu);
+  sage::g_table[sage::Key{kind, sage::bucket(rows), N, K}] = sage::GemmCfg{bn, stages};
+  return SAGE_OK;
+}
+
 extern "C" sage_status sage_tuning_save(const char* path) {
   if (!path) return sage::set_last_error("null path"), SAGE_ERR_INVALID;
   FILE* f = fopen(path, "w");

@@ -395,3 +395,31 @@ def test_host_cache_respects_its_budget():
         assert st["demotions"] == 0 and st["host_cache_entries"] == 0
     finally:
         p.destroy()
+
+
+@pytest.mark.parametrize("tile", [(128, 3), (64, 4), (64, 2), (128, 103), (64, 104)])
+def test_fp32_presplit_tile_configurations_bitwise(pool, tile):
+    """Every configuration of the fp32 pre-split GEMM (incl. the persistent, double-buffered
+    ones) gives the same bits as the default, and matches the oracle."""
+    torch = _torch()
+    spec = workload.spec_tiny(key="rt_pre_%d_%d" % tile, dtype="f32", n_tables=4, rows=3000, dim=64,
+                              bot=(128, 64), top=(256, 128, 1), l_min=0, l_max=30)
+    f = prepare(pool, spec, max_batch=3000)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=600 + i) for i, B in enumerate([900, 1100, 13])]
+        ref = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in ref])
+        torch.cuda.synchronize()
+        M = sum(v["batch"] for v in invs)
+        for (K, N) in [(128, 64), (320, 256), (256, 128)]:
+            if N % tile[0] == 0:
+                sage.tuning_set(3, M, N, K, tile[0], tile[1])
+        got = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in got])
+        torch.cuda.synchronize()
+        f.check_errors()
+        for a, b in zip(ref, got):
+            assert torch.equal(a.out, b.out)
+        _check_inv(spec, workload.weights_arrays(spec), got[0], RTOL["f32"])
+    finally:
+        f.release()
