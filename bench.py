@@ -184,7 +184,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- cold setup: context + pool, prepare (staging beside kernel load / workspace), first invoke
     t0 = time.perf_counter()
-    pool = sage.Pool(device=dev)
+    pool = sage.Pool(device=dev, graphs=True)
     t_pool = time.perf_counter()
     kw = workload.prepare_kwargs(spec)
     fn = pool.prepare(**kw, max_batch=max(4096, M), workspace_slots=2)
@@ -298,6 +298,31 @@ def run_ours(args, rank, world, local_rank):
     plain_times = timed(step_plain, max(3, args.steps // 4))
     plain_rate = n_inv * len(plain_times) / (sum(plain_times) / 1e3)
 
+    # the same fused and plain steps with direct launches instead of CUDA-graph replay
+    gpool = sage.Pool(device=dev, graphs=False)
+    gfn = gpool.prepare(**kw, max_batch=max(4096, M), workspace_slots=2)
+    gfn.wait()
+
+    def gstep_fused():
+        gfn.invoke_batch(args_all, stream=stream)
+
+    def gstep_plain():
+        for a in args_all:
+            gfn.invoke(*a[:5], stream=stream, num_indices=a[5])
+
+    for _ in range(args.warmup):
+        gstep_fused()
+    g_times = timed(gstep_fused, args.steps)
+    for _ in range(max(1, args.warmup // 2)):
+        gstep_plain()
+    gp_times = timed(gstep_plain, max(3, args.steps // 4))
+    graphs_res = {"fused_invocations_per_s": round(n_inv * len(g_times) / (sum(g_times) / 1e3) * world, 2),
+                  "fused_ms_per_step": round(sum(g_times) / len(g_times), 4),
+                  "plain_invocations_per_s": round(n_inv * len(gp_times) / (sum(gp_times) / 1e3) * world, 2),
+                  "note": "same steps, kernels launched one by one instead of one CUDA-graph launch per batch"}
+    gfn.release()
+    gpool.destroy()
+
     # per-kernel timing (events on the launching stream), same fused steps
     sage.profile_enable(True)
     sage.profile_read()
@@ -406,6 +431,7 @@ def run_ours(args, rank, world, local_rank):
                   "ms_per_step": round(sum(plain_times) / len(plain_times), 4),
                   "note": "same invocations, one launch chain per invocation"},
         "speedup_fused_vs_plain": round(value / (plain_rate * world), 3),
+        "direct_launches": graphs_res,
         "setup": setup,
         "tuning": [{"kind": "bf16" if t[0] == "1" else "f32x3tf32", "m_bucket": int(t[1]), "N": int(t[2]),
                     "K": int(t[3]), "bn": int(t[4]), "stages": int(t[5])} for t in tuning],

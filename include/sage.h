@@ -96,6 +96,9 @@ typedef struct {
                                       used images evicted) and a later prepare of the key re-stages
                                       from there at link speed instead of calling its producer.
                                       0 = off (release frees everything). */
+    int graphs;                    /* 1 = sage_invoke / sage_invoke_batch capture each batch's launch
+                                      chain into a CUDA graph (updated in place while the kernels stay
+                                      the same) and launch it in one call; 0 = direct launches */
 } sage_pool_config;
 
 /* Producer of a data item: fill bytes [offset, offset+bytes) of the item into the

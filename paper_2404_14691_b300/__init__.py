@@ -206,13 +206,13 @@ class Pool:
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, staging_chunk_bytes: int = 0,
                  staging_chunks: int = 0, producer_threads: int = 0, serial_setup: bool = False,
-                 torch_allocator: bool = False, host_cache_bytes: int = 0):
+                 torch_allocator: bool = False, host_cache_bytes: int = 0, graphs: bool = False):
         self._hooks = torch_allocator_hooks(device) if torch_allocator else None
         cfg = PoolConfig(device, budget_bytes, staging_chunk_bytes, staging_chunks, producer_threads,
                          1 if serial_setup else 0,
                          ctypes.cast(self._hooks[0], ctypes.c_void_p) if self._hooks else None,
                          ctypes.cast(self._hooks[1], ctypes.c_void_p) if self._hooks else None, None,
-                         int(host_cache_bytes))
+                         int(host_cache_bytes), 1 if graphs else 0)
         h = ctypes.c_void_p()
         check(lib().sage_pool_create(ctypes.byref(cfg), ctypes.byref(h)), "sage_pool_create")
         self.handle = h

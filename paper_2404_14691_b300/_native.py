@@ -29,7 +29,7 @@ class PoolConfig(ctypes.Structure):
                 ("staging_chunk_bytes", ctypes.c_size_t), ("staging_chunks", ctypes.c_int),
                 ("producer_threads", ctypes.c_int), ("serial_setup", ctypes.c_int),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
-                ("host_cache_bytes", ctypes.c_size_t)]
+                ("host_cache_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int)]
 
 
 class DataDesc(ctypes.Structure):

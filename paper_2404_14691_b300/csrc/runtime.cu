@@ -196,6 +196,10 @@ struct Slot {
   // so that they overlap the compute still running on the launch stream
   cudaStream_t h2d = nullptr;
   cudaEvent_t copied = nullptr;
+  // CUDA graph of the launch chain: captured on `capture` for every batch, used to
+  // update `exec` (same kernels, new parameters), which is launched in one call
+  cudaStream_t capture = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 }  // namespace
@@ -273,6 +277,7 @@ struct sage_pool_s {
   sage_dev_free_fn dfree = nullptr;
   void* actx = nullptr;
   bool serial_setup = false;
+  bool graphs = false;           // fused batches replayed through CUDA graphs
   cudaStream_t side = nullptr;   // staging copies
   cudaStream_t alloc = nullptr;  // allocations and frees (never waits behind staging copies)
   size_t chunk_bytes = 0;
@@ -639,6 +644,8 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
       cudaStreamDestroy(s.h2d);
     }
     if (s.copied) cudaEventDestroy(s.copied);
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.capture) cudaStreamDestroy(s.capture);
   }
   // stage 2 of the multi-stage exit: keep the read-only data in the host cache
   bool ok_data = false;
@@ -865,14 +872,51 @@ sage_status acquire_slot(Entry* e, int M, cudaStream_t stream, Slot** out, int w
   return SAGE_OK;
 }
 
+// Capture the launch chain of one batch into the slot's graph executable (update
+// in place when the kernels are the same as last time, else re-instantiate).
+sage_status capture_chain(Entry* e, Slot& s, const InvTable& tab) {
+  SAGE_CK(cudaStreamBeginCapture(s.capture, cudaStreamCaptureModeThreadLocal));
+  sage_status st = launch_chain(e, s, tab, s.capture);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s.capture, &graph);
+  if (st != SAGE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (ce != cudaSuccess) return fail(SAGE_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ce));
+  bool updated = false;
+  if (s.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    updated = cudaGraphExecUpdate(s.exec, graph, &info) == cudaSuccess;
+    if (!updated) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(s.exec);
+      s.exec = nullptr;
+    }
+  }
+  if (!updated) ce = cudaGraphInstantiate(&s.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ce != cudaSuccess) {
+    s.exec = nullptr;
+    return fail(SAGE_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+  }
+  return SAGE_OK;
+}
+
 sage_status run_batch(Entry* e, const InvTable& tab, cudaStream_t stream) {
   std::lock_guard<std::mutex> g(e->imu);
   Slot* s = nullptr;
   sage_status st = acquire_slot(e, tab.M, stream, &s);
   if (st != SAGE_OK) return st;
   SAGE_CK(cudaStreamWaitEvent(stream, e->ready, 0));
-  st = launch_chain(e, *s, tab, stream);
-  if (st != SAGE_OK) return st;
+  if (e->pool->graphs && !g_prof_on.load(std::memory_order_relaxed)) {
+    st = capture_chain(e, *s, tab);
+    if (st != SAGE_OK) return st;
+    SAGE_CK(cudaGraphLaunch(s->exec, stream));
+  } else {
+    st = launch_chain(e, *s, tab, stream);
+    if (st != SAGE_OK) return st;
+  }
   SAGE_CK(cudaEventRecord(s->done, stream));
   s->used = true;
   return SAGE_OK;
@@ -954,6 +998,7 @@ sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
   P->actx = c.alloc_ctx;
   P->serial_setup = c.serial_setup != 0;
   P->host_budget = c.host_cache_bytes;
+  P->graphs = c.graphs != 0;
   size_t free_b = 0, total_b = 0;
   SAGE_CK(cudaMemGetInfo(&free_b, &total_b));
   const size_t margin = size_t(2) << 30;
@@ -1181,6 +1226,7 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.h2d, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming);
     if (ce != cudaSuccess) return setup_failed(fail(SAGE_ERR_CUDA, "event: %s", cudaGetErrorString(ce)));
   }

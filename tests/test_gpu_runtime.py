@@ -423,3 +423,33 @@ def test_fp32_presplit_tile_configurations_bitwise(pool, tile):
         _check_inv(spec, workload.weights_arrays(spec), got[0], RTOL["f32"])
     finally:
         f.release()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_cuda_graph_replay_equals_direct_launches(dtype):
+    """Batches replayed through the captured CUDA graph (updated in place between batches
+    of different sizes) give the same bits as direct launches."""
+    torch = _torch()
+    spec = spec_small(dtype, key="rt_graph_" + dtype)
+    pd, pg = sage.Pool(device=0), sage.Pool(device=0, graphs=True)
+    try:
+        fd, fg = prepare(pd, spec), prepare(pg, spec)
+        for round_ in range(3):
+            sizes = [[300, 7, 55], [1], [128, 256, 1, 900]][round_]
+            invs = [workload.make_invocation(spec, B, seed=700 + 10 * round_ + i) for i, B in enumerate(sizes)]
+            a = [DevInvocation(v) for v in invs]
+            b = [DevInvocation(v) for v in invs]
+            fd.invoke_batch([d.args() for d in a])
+            fg.invoke_batch([d.args() for d in b])
+            c = DevInvocation(invs[0])
+            fg.invoke(*c.args())
+            torch.cuda.synchronize()
+            for x, y in zip(a, b):
+                assert torch.equal(x.out, y.out)
+            assert torch.equal(a[0].out, c.out)
+        fg.check_errors()
+        fd.release()
+        fg.release()
+    finally:
+        pd.destroy()
+        pg.destroy()
