@@ -133,6 +133,143 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tmem_dealloc(tmem, BN);
 }
 
+// Persistent form: one CTA per SM walks the output tiles (n fastest); two TMEM
+// accumulators alternate so the epilogue of tile i overlaps the MMAs of tile i+1;
+// the shared-memory ring runs on across tiles.  warp 0 lane 0: TMA; warp 1 lane 0:
+// MMA; warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
+template <int BN, int NST>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                              int M, int N, int K, const float* __restrict__ bias, int relu,
+                              __nv_bfloat16* __restrict__ Y, int ldy, int* err) {
+  using C = TcCfg<BN, NST>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + C::STAGES * C::A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + C::STAGES * C::B_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* acc_full = empty + C::STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int KB = (K + kBK - 1) / kBK;
+  const int NT = N / BN, MT = (M + kBM - 1) / kBM;
+  const int tiles = NT * MT;
+
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * BN);
+  if (warp == 1 && lane == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 2 && lane == 0) {
+    tma_prefetch_desc(&tmA);
+    tma_prefetch_desc(&tmB);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % C::STAGES;
+          const uint32_t ph = (g / C::STAGES) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], C::STAGE);
+          tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * kBK, m0, &full[s]);
+          tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * kBK, n0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
+      uint32_t g = 0;
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        const int buf = i & 1;
+        const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
+        if (!mbar_wait(&acc_empty[buf], ((i >> 1) & 1) ^ 1, err)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % C::STAGES;
+          const uint32_t ph = (g / C::STAGES) & 1;
+          if (!mbar_wait(&full[s], ph, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + s * C::A_BYTES);
+          const uint32_t b0 = smem_u32(sB + s * C::B_BYTES);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            tc_mma_bf16(acc, sw128_kmajor_desc(a0 + k * 32), sw128_kmajor_desc(b0 + k * 32), idesc,
+                        (kb | k) != 0 ? 1u : 0u);
+          tc_commit(&empty[s]);
+        }
+        tc_commit(&acc_full[buf]);
+      }
+    }
+  } else {
+    const int q = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
+      tc_fence_after();
+      const int row = m0 + q * 32 + lane;
+      __nv_bfloat16* yrow = Y + static_cast<size_t>(row < M ? row : 0) * ldy + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        tmem_ld_wait();
+        if (row < M) {
+          uint32_t pk[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float f0 = __uint_as_float(v[2 * j]) + __ldg(bias + n0 + c0 + 2 * j);
+            float f1 = __uint_as_float(v[2 * j + 1]) + __ldg(bias + n0 + c0 + 2 * j + 1);
+            if (relu) {
+              f0 = fmaxf(f0, 0.f);
+              f1 = fmaxf(f1, 0.f);
+            }
+            pk[j] = pack_bf16x2(f0, f1);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(yrow + c0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) dst[u] = make_uint4(pk[4 * u], pk[4 * u + 1], pk[4 * u + 2], pk[4 * u + 3]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
 // Row-major bf16 matrix [rows, cols] with row stride ld elements, tiles of
 // box_rows x 64 columns, 128-byte swizzle, zero fill outside the matrix.
 bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows) {
@@ -158,10 +295,38 @@ cudaError_t launch_bn(int M, int N, int K, const void* x, int ldx, const void* W
   return cudaGetLastError();
 }
 
+int g_sms_pt = 0;
+
+template <int BN, int NST>
+cudaError_t launch_persistent_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias,
+                                 int relu, void* y, int ldy, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_persistent_kernel<BN, NST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (!g_sms_pt) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_pt, cudaDevAttrMultiProcessorCount, dev);
+  }
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
+  const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
+  const int grid = tiles < g_sms_pt ? tiles : g_sms_pt;
+  gemm_tc_persistent_kernel<BN, NST><<<grid, 192, TcCfg<BN, NST>::SMEM, s>>>(
+      ta, tb, M, N, K, bias, relu, static_cast<__nv_bfloat16*>(y), ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
 // Tile shapes the bf16 GEMM can run: (BN, stages).  The deep pipelines use
 // 192 KB of shared memory (one CTA per SM); the shallow ones ~100 KB (two CTAs
 // per SM, so one CTA's epilogue overlaps the other's main loop).
-const GemmCfg kBf16Cfgs[] = {{256, 4}, {128, 6}, {64, 8}, {256, 2}, {128, 3}, {64, 4}};
+const GemmCfg kBf16Cfgs[] = {{256, 4}, {128, 6}, {64, 8}, {256, 2}, {128, 3}, {64, 4},
+                              {256, 104}, {128, 106}};  // stages >= 100: persistent
 
 cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const void* x, int ldx, const void* W, const float* bias,
                        int relu, void* y, int ldy, int* err, cudaStream_t s) {
@@ -171,6 +336,10 @@ cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const void* x, int ldx, c
   if (c.bn == 256 && c.stages == 2) return launch_bn<256, 2>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   if (c.bn == 128 && c.stages == 3) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   if (c.bn == 64 && c.stages == 4) return launch_bn<64, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 256 && c.stages == 104)
+    return launch_persistent_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (c.bn == 128 && c.stages == 106)
+    return launch_persistent_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return cudaErrorInvalidValue;
 }
 
@@ -214,6 +383,8 @@ void preload_tc_kernels() {
   cudaFuncGetAttributes(&fa, gemm_tc_kernel<256, 2>);
   cudaFuncGetAttributes(&fa, gemm_tc_kernel<128, 3>);
   cudaFuncGetAttributes(&fa, gemm_tc_kernel<64, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tc_persistent_kernel<256, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tc_persistent_kernel<128, 6>);
   encode_fn();
 }
 

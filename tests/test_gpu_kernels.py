@@ -211,7 +211,7 @@ def test_linear_rejects_unsupported_shapes():
                     y.data_ptr(), 64)
 
 
-BF16_TILES = [(256, 4), (128, 6), (64, 8), (256, 2), (128, 3), (64, 4)]
+BF16_TILES = [(256, 4), (128, 6), (64, 8), (256, 2), (128, 3), (64, 4), (256, 104), (128, 106)]
 F32_TILES = [(128, 3), (64, 4), (64, 2)]
 
 
