@@ -70,6 +70,26 @@ def n_indices(invs):
     return int(sum(v["indices"].size for v in invs))
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(x: float) -> float:
+    """Maximum of x over the ranks of the default process group (x itself when not
+    distributed).  Replicas only: this is the one collective, for timing."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -220,9 +240,14 @@ def run_ours(args, rank, world, local_rank):
     # tensor-core tile autotuning for the fused batch and for single-invocation sizes
     tt = time.perf_counter()
     tuning = []
+    if args.load_tuning:
+        sage.tuning_load(args.load_tuning)
     if not args.no_autotune:
         for rows in sorted({M, 128, 256, 512}):
             fn.autotune(rows)
+    if args.save_tuning:
+        sage.tuning_save(args.save_tuning)
+    if not args.no_autotune or args.load_tuning:
         fd, tpath = tempfile.mkstemp(suffix=".txt")
         os.close(fd)
         sage.tuning_save(tpath)
@@ -283,13 +308,9 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = float(sum(times))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(times)))
     ms_per_step = total_ms / args.steps
-    value = world * n_inv * args.steps / (total_ms / 1e3)
+    value = job_rate(n_inv * args.steps, world, total_ms / 1e3)
     fn.check_errors()
 
     # plain form: the same invocations, one launch chain each
@@ -360,11 +381,7 @@ def run_ours(args, rank, world, local_rank):
         fn.invoke_batch_host_async(host_arrays[k % 2], stream=stream)
         submit += time.perf_counter() - t1
     stream.synchronize()
-    e2e_s = time.perf_counter() - e0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - e0)
     h2d = int(h_dense.numel() * 4 + h_idx.numel() * 4 + h_off.numel() * 8)
     d2h = int(M * 4)
     # the e2e outputs equal the device-path outputs
@@ -730,6 +747,8 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--save-tuning", default="", help="write the tile-tuning table to this file")
+    ap.add_argument("--load-tuning", default="", help="load a tile-tuning table before running")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--stress-functions", type=int, default=16)
     ap.add_argument("--stress-invocations", type=int, default=256)
