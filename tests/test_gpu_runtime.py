@@ -453,3 +453,69 @@ def test_cuda_graph_replay_equals_direct_launches(dtype):
     finally:
         pd.destroy()
         pg.destroy()
+
+
+
+def test_more_than_256_invocations_and_empty_members(pool):
+    """A batch above the per-launch table size (256) runs as several fused launches;
+    empty invocations are skipped; every member still equals its isolated invocation."""
+    torch = _torch()
+    spec = spec_small("f32", key="rt_many")
+    f = prepare(pool, spec, max_batch=8192)
+    try:
+        sizes = [(i * 7) % 23 for i in range(300)]          # zeros every 23rd member
+        invs = [workload.make_invocation(spec, B, seed=800 + i) for i, B in enumerate(sizes)]
+        fused = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in fused])
+        f.invoke_batch([])                                   # an empty batch is a no-op
+        picks = [0, 1, 23, 100, 255, 256, 257, 299]          # both sides of the 256 boundary
+        alone = [DevInvocation(invs[k]) for k in picks]
+        for d in alone:
+            f.invoke(*d.args())
+        torch.cuda.synchronize()
+        for k, d in zip(picks, alone):
+            assert torch.equal(fused[k].out[:sizes[k]], d.out[:sizes[k]]), k
+        _check_inv(spec, workload.weights_arrays(spec), fused[257], RTOL["f32"])
+    finally:
+        f.release()
+
+
+@pytest.mark.parametrize("case", ["bf16_hidden_96", "row_96_bytes", "head_2_outputs"])
+def test_invalid_descriptors_are_rejected(pool, case):
+    if case == "bf16_hidden_96":    # a bf16 layer with K = 96 does not tile by 64
+        spec = workload.FunctionSpec(key="rt_bad1", dtype="bf16", rows=[100] * 2, dim=64, bot_dims=[96, 64],
+                                     top_dims=[128, 1], l_min=0, l_max=3)
+    elif case == "row_96_bytes":    # rows must be a power-of-two number of bytes
+        spec = workload.spec_tiny(key="rt_bad2", dtype="f32", dim=24, bot=(16, 24))
+    else:                           # the head is one sigmoid output
+        spec = workload.spec_tiny(key="rt_bad3", dtype="f32", top=(16, 2))
+    before = pool.stats()["functions"]
+    with pytest.raises(sage.SageError) as e:
+        prepare(pool, spec)
+    assert e.value.status == -1
+    assert pool.stats()["functions"] == before
+
+
+def test_bounded_wait_times_out_then_completes(pool):
+    spec = spec_small("bf16", key="rt_timeout")
+    ctx, keep = workload.tables_ctx(spec)
+    real = workload.lib().wl_fill_tables
+
+    @workload.FILL_FN
+    def slow_fill(dst, off, n, c):
+        time.sleep(0.2)
+        return real(dst, off, n, ctypes.addressof(ctx))
+
+    args = workload.prepare_kwargs(spec)
+    args["tables_fill"] = ctypes.cast(slow_fill, ctypes.c_void_p).value
+    args["tables_ctx"] = None
+    args["keep"] = (args["keep"], slow_fill, ctx, keep)
+    f = pool.prepare(**args)
+    try:
+        with pytest.raises(sage.SageError) as e:
+            f.wait(timeout_us=1000)
+        assert e.value.status == -4
+        f.wait()
+        assert f.query() == sage.SAGE_OK
+    finally:
+        f.release()
