@@ -99,6 +99,10 @@ typedef struct {
     int graphs;                    /* 1 = sage_invoke / sage_invoke_batch capture each batch's launch
                                       chain into a CUDA graph (updated in place while the kernels stay
                                       the same) and launch it in one call; 0 = direct launches */
+    int exportable;                /* 1 = read-only items are allocated as exportable physical memory
+                                      (CUDA virtual memory management, POSIX file-descriptor handles)
+                                      so that sage_share_start can map them into other processes;
+                                      dev_alloc is then used for workspaces only */
 } sage_pool_config;
 
 /* Producer of a data item: fill bytes [offset, offset+bytes) of the item into the
@@ -339,6 +343,9 @@ typedef struct {
     int lanes_per_fn;              /* concurrent batches per function; 0 = 2 */
     double linger_s;               /* keep an idle function resident this long; < 0 = until evicted */
     double timeout_s;              /* give up after this long (SAGE_ERR_TIMEOUT); 0 = 600 */
+    int sm_partition;              /* 1 = each function's lanes run in its own SM partition (one green
+                                      context per function, SMs / n_fns each, see sage_partition_create);
+                                      0 = all functions share every SM */
 } sage_serve_config;
 
 typedef struct {
@@ -419,6 +426,88 @@ sage_status sage_linear(sage_dtype dtype, int M, int N, int K, const void* x, in
 sage_status sage_linear_tiled(sage_dtype dtype, int M, int N, int K, const void* x, int ldx, const void* W,
                               const float* bias, int act, void* y, int ldy, int bn, int stages, int* err_word,
                               void* stream);
+
+/* ---------------------------------------------------------------- cross-process sharing
+ *
+ * The paper's memory daemon is a separate process: a function's engine hands it
+ * the data request first, and the daemon loads the data while the engine creates
+ * the GPU context, the two in parallel (Sec. 3.1, Sec. 4.1); all invocations of a
+ * function on a GPU share the daemon's one read-only copy (Sec. 5.2).  Here:
+ *
+ *   owner process : pool created with exportable = 1; sage_share_start serves the
+ *                   functions given to sage_share_register on a UNIX socket;
+ *   function process : sage_attach_begin (no CUDA call: it only sends the request,
+ *                   and the owner starts staging at once), then its own context
+ *                   (sage_pool_create), then sage_attach_end, which maps the owner's
+ *                   copy and returns before the data is complete.  Invocations wait
+ *                   for the owner's "complete" word exactly as for local staging.
+ *
+ * Each attached handle holds one reference in the owner's pool until it is
+ * released, or its process exits (the socket closes); the owner stages a key
+ * once however many processes attach.  The read-only copy is mapped read-write
+ * in the function process; the functions here only read it.  Both processes must
+ * use the same physical GPU (checked by UUID). */
+typedef struct sage_share_s* sage_share;
+typedef struct sage_ticket_s* sage_ticket;
+
+typedef struct {
+    int64_t connections;   /* attach requests received */
+    int64_t grants;        /* requests answered with a mapping */
+    int64_t rejects;       /* requests refused (unknown key, other shape, failed prepare) */
+    int64_t ready;         /* "data complete" words sent */
+    int64_t releases;      /* references returned (release or disconnect) */
+    int64_t active;        /* attached references held now */
+} sage_share_stats;
+
+/* Serve `pool`'s functions to other processes on the UNIX socket `socket_path`
+ * (created; an existing file of that name is replaced).  The pool must be
+ * exportable.  SAGE_ERR_INVALID for a non-exportable pool or a path longer than
+ * 107 bytes; SAGE_ERR_CUDA when the socket cannot be created. */
+sage_status sage_share_start(sage_pool pool, const char* socket_path, sage_share* out);
+/* Make a function attachable by key.  The descriptor (with its data sources) is
+ * copied; its producer contexts and host images must stay valid until
+ * sage_share_stop.  The owner prepares the key on the first attach request. */
+sage_status sage_share_register(sage_share share, const sage_fn_desc* desc);
+sage_status sage_share_stats_get(sage_share share, sage_share_stats* out);
+/* Stop serving: closes the socket, returns every attached reference (the owner's
+ * copy stays mapped in processes that still use it until they release it). */
+sage_status sage_share_stop(sage_share share);
+
+/* Send an attach request for `shape` (data sources ignored) to the owner at
+ * `socket_path`.  Makes no CUDA call.  SAGE_ERR_INVALID for a bad shape or when no
+ * owner listens there. */
+sage_status sage_attach_begin(const char* socket_path, const sage_fn_desc* shape, sage_ticket* out);
+/* Complete an attach in `pool` (consumes the ticket, also on failure): receives
+ * the owner's answer, maps its copy, builds this process's workspaces and returns
+ * the handle (refcount semantics as sage_prepare; a key this pool already holds is
+ * shared locally).  The owner's refusal status is returned as is (SAGE_ERR_INVALID
+ * for an unknown key or another shape, SAGE_ERR_NOMEM, ...); SAGE_ERR_INVALID when
+ * the owner uses another GPU; SAGE_ERR_CUDA when the mapping fails;
+ * SAGE_ERR_TIMEOUT when the owner does not answer within 60 s.  A staging failure
+ * in the owner makes the handle sticky-failed (SAGE_ERR_STAGING). */
+sage_status sage_attach_end(sage_pool pool, sage_ticket ticket, sage_fn* out);
+/* Drop a ticket without completing it (closes the request; the owner returns any
+ * reference it took).  Makes no CUDA call. */
+sage_status sage_attach_cancel(sage_ticket ticket);
+
+/* ---------------------------------------------------------------- SM partitions
+ *
+ * Functions served side by side on one GPU compete for its SMs; the paper lists
+ * partitioning the SMs between functions among its lessons (Sec. 7.10).  A
+ * partition splits the device's SMs into `groups` equal groups (green contexts)
+ * of min_sms SMs each, rounded up to the hardware's partition granularity, or,
+ * with min_sms = 0, of SMs / groups rounded down to it.  Kernels launched on a group's stream
+ * run only on that group's SMs; sage_invoke* on such a stream keeps the whole
+ * launch chain on it (no bottom-MLP branch stream, no CUDA graph), so every
+ * kernel of the function stays inside the group.  SAGE_ERR_INVALID when the SMs
+ * cannot hold the groups; SAGE_ERR_CUDA when green contexts are unavailable. */
+typedef struct sage_partition_s* sage_partition;
+sage_status sage_partition_create(int device, int groups, int min_sms, sage_partition* out);
+int sage_partition_groups(sage_partition p);
+/* Group g's stream (a cudaStream_t owned by the partition) and its SM count. */
+sage_status sage_partition_stream(sage_partition p, int group, void** stream, int* sms);
+/* Waits for the groups' streams, then destroys them and the green contexts. */
+sage_status sage_partition_destroy(sage_partition p);
 
 #ifdef __cplusplus
 }

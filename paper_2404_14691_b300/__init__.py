@@ -15,10 +15,11 @@ from typing import Optional, Sequence
 
 from ._native import (DEV_ALLOC_FN, DEV_FREE_FN, SAGE_BF16, SAGE_F32, SAGE_OK, SAGE_PENDING, SAGE_READONLY,
                       STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, KernelTime, PoolConfig, PoolStats,
-                      Request, RequestResult, SageError, ServeConfig, ServeStats, check, lib)
+                      Request, RequestResult, SageError, ServeConfig, ServeStats, ShareStats, check, lib)
 
 __all__ = ["Pool", "Function", "SageError", "SAGE_F32", "SAGE_BF16", "embedding_bag_sum", "linear",
-           "kernel_launches", "profile_enable", "profile_read", "torch_allocator_hooks", "serve"]
+           "kernel_launches", "profile_enable", "profile_read", "torch_allocator_hooks", "serve", "Share",
+           "attach_begin", "Partition"]
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -115,7 +116,8 @@ def fn_desc(key: str, dtype: int, rows: Sequence[int], dim: int, n_dense: int, b
 
 
 def serve(pool: "Pool", functions: Sequence[dict], requests: Sequence[tuple], max_batch_invocations: int = 0,
-          max_batch_rows: int = 0, lanes_per_fn: int = 0, linger_s: float = -1.0, timeout_s: float = 0.0):
+          max_batch_rows: int = 0, lanes_per_fn: int = 0, linger_s: float = -1.0, timeout_s: float = 0.0,
+          sm_partition: bool = False):
     """Replay a request trace with continuous batching (sage_serve).
 
     functions: fn_desc keyword dicts; requests: (fn, arrival_s, batch, dense, indices, offsets,
@@ -127,7 +129,8 @@ def serve(pool: "Pool", functions: Sequence[dict], requests: Sequence[tuple], ma
                                        for (f, t, b, d, i, o, ni, u) in requests])
     res = (RequestResult * max(1, len(requests)))()
     st = ServeStats()
-    cfg = ServeConfig(max_batch_invocations, max_batch_rows, lanes_per_fn, linger_s, timeout_s)
+    cfg = ServeConfig(max_batch_invocations, max_batch_rows, lanes_per_fn, linger_s, timeout_s,
+                      1 if sm_partition else 0)
     check(lib().sage_serve(pool.handle, arr, len(descs), reqs, len(requests), ctypes.byref(cfg), res,
                            ctypes.byref(st)), "sage_serve")
     out = [{name: getattr(res[k], name) for name, _ in RequestResult._fields_} for k in range(len(requests))]
@@ -206,13 +209,14 @@ class Pool:
 
     def __init__(self, device: int = 0, budget_bytes: int = 0, staging_chunk_bytes: int = 0,
                  staging_chunks: int = 0, producer_threads: int = 0, serial_setup: bool = False,
-                 torch_allocator: bool = False, host_cache_bytes: int = 0, graphs: bool = False):
+                 torch_allocator: bool = False, host_cache_bytes: int = 0, graphs: bool = False,
+                 exportable: bool = False):
         self._hooks = torch_allocator_hooks(device) if torch_allocator else None
         cfg = PoolConfig(device, budget_bytes, staging_chunk_bytes, staging_chunks, producer_threads,
                          1 if serial_setup else 0,
                          ctypes.cast(self._hooks[0], ctypes.c_void_p) if self._hooks else None,
                          ctypes.cast(self._hooks[1], ctypes.c_void_p) if self._hooks else None, None,
-                         int(host_cache_bytes), 1 if graphs else 0)
+                         int(host_cache_bytes), 1 if graphs else 0, 1 if exportable else 0)
         h = ctypes.c_void_p()
         check(lib().sage_pool_create(ctypes.byref(cfg), ctypes.byref(h)), "sage_pool_create")
         self.handle = h
@@ -223,6 +227,16 @@ class Pool:
         h = ctypes.c_void_p()
         check(lib().sage_prepare(self.handle, ctypes.byref(d), ctypes.byref(h)), "sage_prepare")
         return Function(self, h.value, keep)
+
+    def attach(self, ticket: "Ticket") -> Function:
+        """Complete an attach begun with attach_begin (sage_attach_end): map the
+        owner's read-only copy into this process; returns before it is complete."""
+        h = ctypes.c_void_p()
+        t, ticket.handle = ticket.handle, None
+        if t is None:
+            raise ValueError("ticket already used")
+        check(lib().sage_attach_end(self.handle, t, ctypes.byref(h)), "sage_attach_end")
+        return Function(self, h.value, ticket._keep)
 
     def stats(self) -> dict:
         s = PoolStats()
@@ -266,3 +280,82 @@ def linear(dtype: int, M: int, N: int, K: int, x: int, ldx: int, W: int, bias: i
     else:
         check(lib().sage_linear_tiled(dtype, M, N, K, x, ldx, W, bias, 1 if relu else 0, y, ldy, int(tile[0]),
                                       int(tile[1]), err_word, _stream_handle(stream)), "sage_linear_tiled")
+
+
+class Share:
+    """Serve an exportable pool's functions to other processes (sage_share_start)."""
+
+    def __init__(self, pool: Pool, socket_path: str):
+        h = ctypes.c_void_p()
+        check(lib().sage_share_start(pool.handle, socket_path.encode(), ctypes.byref(h)), "sage_share_start")
+        self.handle = h
+        self._keep = []
+
+    def register(self, **kw) -> None:
+        """Make a function attachable (keyword arguments of fn_desc, with its data sources,
+        which stay referenced until stop())."""
+        d, keep = fn_desc(**kw)
+        check(lib().sage_share_register(self.handle, ctypes.byref(d)), "sage_share_register")
+        self._keep.append((d, keep))
+
+    def stats(self) -> dict:
+        s = ShareStats()
+        check(lib().sage_share_stats_get(self.handle, ctypes.byref(s)), "sage_share_stats_get")
+        return {name: getattr(s, name) for name, _ in ShareStats._fields_}
+
+    def stop(self) -> None:
+        if self.handle is not None:
+            check(lib().sage_share_stop(self.handle), "sage_share_stop")
+            self.handle = None
+            self._keep = []
+
+
+class Ticket:
+    """An attach request in flight (sage_attach_begin); completed by Pool.attach."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def cancel(self) -> None:
+        """Drop the request without completing it (sage_attach_cancel)."""
+        if self.handle is not None:
+            h, self.handle = self.handle, None
+            check(lib().sage_attach_cancel(h), "sage_attach_cancel")
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None:
+            lib().sage_attach_cancel(self.handle)
+            self.handle = None
+
+
+def attach_begin(socket_path: str, **kw) -> Ticket:
+    """Send an attach request for a function shape to the owner at socket_path.  Makes no
+    CUDA call, so a new process can send it before creating its context."""
+    d, keep = fn_desc(**kw)
+    h = ctypes.c_void_p()
+    check(lib().sage_attach_begin(socket_path.encode(), ctypes.byref(d), ctypes.byref(h)), "sage_attach_begin")
+    return Ticket(h, keep)
+
+
+class Partition:
+    """SM partition of a GPU (sage_partition_create): `groups` green contexts, each
+    with a stream whose kernels run on the group's SMs only."""
+
+    def __init__(self, device: int = 0, groups: int = 2, min_sms: int = 0):
+        h = ctypes.c_void_p()
+        check(lib().sage_partition_create(device, groups, min_sms, ctypes.byref(h)), "sage_partition_create")
+        self.handle = h
+        self.groups = lib().sage_partition_groups(h)
+
+    def stream(self, group: int):
+        """(stream handle, SM count) of a group."""
+        s, n = ctypes.c_void_p(), ctypes.c_int()
+        check(lib().sage_partition_stream(self.handle, group, ctypes.byref(s), ctypes.byref(n)),
+              "sage_partition_stream")
+        return s.value, n.value
+
+    def destroy(self) -> None:
+        if self.handle is not None:
+            check(lib().sage_partition_destroy(self.handle), "sage_partition_destroy")
+            self.handle = None

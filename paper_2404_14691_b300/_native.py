@@ -29,7 +29,7 @@ class PoolConfig(ctypes.Structure):
                 ("staging_chunk_bytes", ctypes.c_size_t), ("staging_chunks", ctypes.c_int),
                 ("producer_threads", ctypes.c_int), ("serial_setup", ctypes.c_int),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
-                ("host_cache_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int)]
+                ("host_cache_bytes", ctypes.c_size_t), ("graphs", ctypes.c_int), ("exportable", ctypes.c_int)]
 
 
 class DataDesc(ctypes.Structure):
@@ -67,7 +67,8 @@ class Request(ctypes.Structure):
 
 class ServeConfig(ctypes.Structure):
     _fields_ = [("max_batch_invocations", ctypes.c_int), ("max_batch_rows", ctypes.c_int64),
-                ("lanes_per_fn", ctypes.c_int), ("linger_s", ctypes.c_double), ("timeout_s", ctypes.c_double)]
+                ("lanes_per_fn", ctypes.c_int), ("linger_s", ctypes.c_double), ("timeout_s", ctypes.c_double),
+                ("sm_partition", ctypes.c_int)]
 
 
 class RequestResult(ctypes.Structure):
@@ -94,6 +95,11 @@ class PoolStats(ctypes.Structure):
                 ("last_workspace_ms", ctypes.c_double), ("last_prepare_ms", ctypes.c_double),
                 ("host_cache_bytes", ctypes.c_size_t), ("host_cache_entries", ctypes.c_int64),
                 ("host_cache_hits", ctypes.c_int64), ("demotions", ctypes.c_int64)]
+
+
+class ShareStats(ctypes.Structure):
+    _fields_ = [("connections", ctypes.c_int64), ("grants", ctypes.c_int64), ("rejects", ctypes.c_int64),
+                ("ready", ctypes.c_int64), ("releases", ctypes.c_int64), ("active", ctypes.c_int64)]
 
 
 # (name, restype, argtypes) of every exported entry point of include/sage.h
@@ -127,6 +133,17 @@ SIGNATURES = [
     ("sage_invoke_noalloc", _i, [ctypes.POINTER(FnDesc), _vp, _vp, ctypes.POINTER(Invocation), _vp]),
     ("sage_embedding_bag_sum", _i, [_i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     ("sage_linear", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp]),
+    ("sage_share_start", _i, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),
+    ("sage_share_register", _i, [_vp, ctypes.POINTER(FnDesc)]),
+    ("sage_share_stats_get", _i, [_vp, ctypes.POINTER(ShareStats)]),
+    ("sage_share_stop", _i, [_vp]),
+    ("sage_attach_begin", _i, [ctypes.c_char_p, ctypes.POINTER(FnDesc), ctypes.POINTER(_vp)]),
+    ("sage_attach_end", _i, [_vp, _vp, ctypes.POINTER(_vp)]),
+    ("sage_attach_cancel", _i, [_vp]),
+    ("sage_partition_create", _i, [_i, _i, _i, ctypes.POINTER(_vp)]),
+    ("sage_partition_groups", _i, [_vp]),
+    ("sage_partition_stream", _i, [_vp, _i, ctypes.POINTER(_vp), ctypes.POINTER(_i)]),
+    ("sage_partition_destroy", _i, [_vp]),
     ("sage_linear_tiled", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _i, _i, _vp, _vp]),
 ]
 

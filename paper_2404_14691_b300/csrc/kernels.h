@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+#include <vector>
+
 #include <cuda.h>
 
 #include "common.cuh"
@@ -89,5 +92,79 @@ void preload_gather_kernels();
 void preload_simt_kernels();
 void preload_tc_kernels();
 void preload_tf32_kernels();
+
+// ---------------------------------------------------------------- cross-process sharing
+//
+// The read-only copy of a function can live in one process (the owner, whose pool
+// was created exportable) and be mapped by others (Sec. 4.1: the data is prepared
+// by a daemon process while the function process sets up its own context).  The
+// owner allocates that copy as virtual-memory-management (VMM) physical memory
+// that can be exported as a POSIX file descriptor; a client imports the
+// descriptor and maps the same physical memory into its own address space.
+
+// One exportable device allocation: physical handle, its mapping here, mapped size
+// (a multiple of the allocation granularity).
+struct VmmBlock {
+  unsigned long long handle = 0;  // CUmemGenericAllocationHandle
+  void* va = nullptr;
+  size_t size = 0;
+};
+// Allocates >= bytes of exportable device memory on `device`, mapped read-write in
+// this process.  false (and a last-error message) on failure.
+bool vmm_alloc(int device, size_t bytes, VmmBlock* out);
+// Unmaps and releases this process's reference (the physical memory lives on while
+// another process still maps it).
+void vmm_free(VmmBlock& b);
+
+// A function's read-only data mapped from another process.  The client pool owns
+// it through the entry it backs and destroys it after the entry's last use.
+struct ImportedData {
+  char* tables = nullptr;
+  char* weights = nullptr;
+  // Blocks until the owner reports the data complete (true) or failed / the link
+  // closed (false).
+  virtual bool wait_ready() = 0;
+  // Makes a blocked wait_ready() return false (called before the entry is freed).
+  virtual void interrupt() = 0;
+  virtual ~ImportedData() {}
+};
+
+// ---------------------------------------------------------------- SM partitions
+
+// Green contexts splitting the SMs into groups; streams created in a group run
+// their kernels on its SMs only.
+struct Partition {
+  struct Group {
+    CUgreenCtx ctx = nullptr;
+    int sms = 0;
+    std::vector<CUstream> streams;
+  };
+  int device = 0;
+  int total_sms = 0;
+  std::vector<Group> groups;
+  // n groups of min_sms SMs (rounded up to the hardware granularity) or, with
+  // min_sms = 0, of SMs / n rounded down to it.
+  static sage_status create(int device, int n, int min_sms, Partition** out);
+  // A new non-blocking stream in group i (destroyed with the partition).
+  sage_status stream(int i, cudaStream_t* out);
+  ~Partition();
+};
+// True when s belongs to a green context: launch chains on it stay on it (no
+// branch stream, no graph of the primary context).
+bool stream_is_confined(cudaStream_t s);
+
+// Shape checks of a descriptor without its data sources (the attaching side has none).
+sage_status check_shape(const sage_fn_desc* d);
+// The shape signature two sides compare before one maps the other's copy.
+std::string shape_signature(const sage_fn_desc* d);
+// Prepares `shape` in `pool` on data another process owns: like sage_prepare but
+// the read-only items are `imp`'s mappings and "staging" is waiting for the owner.
+// Takes ownership of imp (also on failure).
+sage_status prepare_imported(sage_pool pool, const sage_fn_desc* shape, ImportedData* imp, sage_fn* out);
+// The pool's CUDA ordinal, and whether it allocates exportable read-only items.
+int pool_device(sage_pool pool);
+bool pool_exportable(sage_pool pool);
+// The exportable blocks holding f's tables and weights (the owner's side).
+sage_status fn_export(sage_fn f, VmmBlock* tables, VmmBlock* weights);
 
 }  // namespace sage

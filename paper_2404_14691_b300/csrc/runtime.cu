@@ -239,6 +239,11 @@ struct Entry {
   size_t wsplit_bytes = 0;
   std::vector<std::pair<const float*, const float*>> wplanes;  // per layer: (hi, lo) or nulls
   HostImage owned;        // host image this entry was re-staged from (kept for the next demotion)
+  // read-only items mapped from another process (cross-process sharing): no
+  // staging here; a waiter thread opens the readiness gate when the owner reports
+  // the data complete
+  std::unique_ptr<sage::ImportedData> imp;
+  std::thread imp_waiter;
 
   // staging (the read-only data's journey host -> device)
   sage_data_desc tdesc{}, wdesc{};
@@ -278,6 +283,8 @@ struct sage_pool_s {
   void* actx = nullptr;
   bool serial_setup = false;
   bool graphs = false;           // fused batches replayed through CUDA graphs
+  bool exportable = false;       // read-only items in exportable VMM memory (shared with other processes)
+  std::unordered_map<void*, sage::VmmBlock> vmm;  // exportable blocks by mapped address (under mu)
   cudaStream_t side = nullptr;   // staging copies
   cudaStream_t alloc = nullptr;  // allocations and frees (never waits behind staging copies)
   size_t chunk_bytes = 0;
@@ -315,6 +322,30 @@ struct sage_pool_s {
     if (!p) return;
     if (dfree) dfree(p, bytes, s, actx);
     else cudaFreeAsync(p, s);
+  }
+  // Read-only items (tables, weights): exportable VMM blocks when the pool shares
+  // them with other processes, otherwise ordinary device memory.
+  void* ro_alloc(size_t bytes, cudaStream_t s) {
+    if (!exportable) return dev_alloc(bytes, s);
+    sage::VmmBlock b;
+    if (!sage::vmm_alloc(device, bytes ? bytes : 256, &b)) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    vmm[b.va] = b;
+    return b.va;
+  }
+  // Every use of p must have finished (VMM blocks are unmapped at once).
+  void ro_free(void* p, size_t bytes, cudaStream_t s) {
+    if (!p) return;
+    if (!exportable) return dev_free(p, bytes, s);
+    sage::VmmBlock b;
+    {
+      std::lock_guard<std::mutex> g(mu);
+      auto it = vmm.find(p);
+      if (it == vmm.end()) return;
+      b = it->second;
+      vmm.erase(it);
+    }
+    sage::vmm_free(b);
   }
 };
 
@@ -406,10 +437,9 @@ bool stage_item(sage_pool_s* P, Entry* e, const sage_data_desc& d, char* dst, do
   return true;
 }
 
-void stage_entry(sage_pool_s* P, Entry* e) {
-  double fill_ms = 0;
-  bool ok = stage_item(P, e, e->wdesc, e->d_weights, &fill_ms) &&
-            stage_item(P, e, e->tdesc, e->d_tables, &fill_ms);
+// After the read-only items are in place (or failed): the split weight planes,
+// the ready event and the entry's staging state.
+void finish_staging(sage_pool_s* P, Entry* e, bool ok, double fill_ms) {
   if (ok && e->presplit) {
     for (size_t l = 0; l < e->wplanes.size(); ++l) {
       if (!e->wplanes[l].first) continue;
@@ -433,6 +463,13 @@ void stage_entry(sage_pool_s* P, Entry* e) {
   e->fill_ms = fill_ms;
   e->sstate = ok ? 1 : 2;
   e->scv.notify_all();
+}
+
+void stage_entry(sage_pool_s* P, Entry* e) {
+  double fill_ms = 0;
+  const bool ok = stage_item(P, e, e->wdesc, e->d_weights, &fill_ms) &&
+                  stage_item(P, e, e->tdesc, e->d_tables, &fill_ms);
+  finish_staging(P, e, ok, fill_ms);
 }
 
 void stager_loop(sage_pool_s* P) {
@@ -551,8 +588,9 @@ sage_status build_slot(Entry* e, Slot& s, int cap, cudaStream_t stream) {
   return SAGE_OK;
 }
 
-sage_status check_desc(const sage_fn_desc* d) {
+sage_status check_shape_impl(const sage_fn_desc* d) {
   if (!d || !d->fn_key) return fail(SAGE_ERR_INVALID, "null descriptor or key");
+  if (strlen(d->fn_key) == 0 || strlen(d->fn_key) > 200) return fail(SAGE_ERR_INVALID, "key length must be 1..200");
   if (d->dtype != SAGE_F32 && d->dtype != SAGE_BF16) return fail(SAGE_ERR_INVALID, "bad dtype");
   if (d->num_tables < 1 || d->num_tables > kMaxTables || !d->rows) return fail(SAGE_ERR_INVALID, "bad num_tables");
   const int es = d->dtype == SAGE_BF16 ? 2 : 4;
@@ -571,8 +609,6 @@ sage_status check_desc(const sage_fn_desc* d) {
   if (d->tables.bytes != tb) return fail(SAGE_ERR_INVALID, "tables.bytes %zu != %zu", d->tables.bytes, tb);
   if (d->tables.access != SAGE_READONLY || d->weights.access != SAGE_READONLY)
     return fail(SAGE_ERR_INVALID, "tables and weights must be SAGE_READONLY");
-  if ((!d->tables.host_src) == (!d->tables.fill) || (!d->weights.host_src) == (!d->weights.fill))
-    return fail(SAGE_ERR_INVALID, "each data item needs exactly one of host_src or fill");
   // layer shapes
   std::vector<std::pair<int, int>> L;
   int prev = d->n_dense;
@@ -608,6 +644,14 @@ sage_status check_desc(const sage_fn_desc* d) {
   return SAGE_OK;
 }
 
+sage_status check_desc(const sage_fn_desc* d) {
+  sage_status st = check_shape_impl(d);
+  if (st != SAGE_OK) return st;
+  if ((!d->tables.host_src) == (!d->tables.fill) || (!d->weights.host_src) == (!d->weights.fill))
+    return fail(SAGE_ERR_INVALID, "each data item needs exactly one of host_src or fill");
+  return SAGE_OK;
+}
+
 bool same_shape(const Entry* e, const sage_fn_desc* d) {
   if (e->dtype != d->dtype || e->T != d->num_tables || e->dim != d->dim || e->n_dense != d->n_dense) return false;
   if (static_cast<int>(e->bot.size()) != d->n_bot || static_cast<int>(e->top.size()) != d->n_top) return false;
@@ -622,11 +666,13 @@ bool same_shape(const Entry* e, const sage_fn_desc* d) {
 
 // Free an entry's device memory after all of its work finished.
 void destroy_entry(sage_pool_s* P, Entry* e) {
+  if (e->imp) e->imp->interrupt();  // a waiter still blocked on the owner returns (failed)
   {
     std::unique_lock<std::mutex> l(e->smu);
     e->cancel = true;
     e->scv.wait(l, [&] { return e->sstate != 0; });
   }
+  if (e->imp_waiter.joinable()) e->imp_waiter.join();
   if (e->ready) cudaEventSynchronize(e->ready);
   for (auto& s : e->slots) {
     if (s.done) {
@@ -651,7 +697,7 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
   bool ok_data = false;
   {
     std::lock_guard<std::mutex> g(e->smu);
-    ok_data = e->sstate == 1 && e->setup == 1;
+    ok_data = e->sstate == 1 && e->setup == 1 && !e->imp;  // imported data is the owner's to keep
   }
   if (P->host_budget > 0 && ok_data) {
     std::unique_lock<std::mutex> g(P->mu);
@@ -701,11 +747,14 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
     P->dev_free(s.buf, s.bytes, P->alloc);
     P->dev_free(s.io, s.io_bytes, P->alloc);
   }
-  P->dev_free(e->d_tables, e->tables_bytes, P->alloc);
-  P->dev_free(e->d_weights, e->weights_bytes, P->alloc);
+  if (!e->imp) {
+    P->ro_free(e->d_tables, e->tables_bytes, P->alloc);
+    P->ro_free(e->d_weights, e->weights_bytes, P->alloc);
+  }
   P->dev_free(e->d_wsplit, e->wsplit_bytes, P->alloc);
   P->dev_free(e->d_err, 256, P->alloc);
   cudaStreamSynchronize(P->alloc);
+  e->imp.reset();  // unmap the owner's copy after the last use above
   if (e->ready) cudaEventDestroy(e->ready);
   {
     std::lock_guard<std::mutex> g(P->mu);
@@ -740,7 +789,7 @@ int f32_kind(int N, int K, int ldx, int ldy) {
   return f32_on_tensor_cores(N, K, ldx, ldy) ? kProfGemmTf32 : kProfGemmF32;
 }
 
-sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t stream) {
+sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t stream, bool confined = false) {
   const int M = tab.M;
   const int nb = static_cast<int>(e->bot.size()), nt = static_cast<int>(e->top.size());
   const size_t es = e->elem();
@@ -760,8 +809,9 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   // fork: the bottom MLP (columns [T*dim, cd) of the concat buffer) runs on the
   // slot's branch stream while the gather (columns [0, T*dim)) runs on `stream`
   // (while kernel timing is on, the branch is serialised so that each kernel's
-  // events measure it alone)
-  const bool overlap = !g_prof_on.load(std::memory_order_relaxed);
+  // events measure it alone; on a confined stream -- an SM partition -- it stays
+  // on that stream so that every kernel runs on the partition's SMs)
+  const bool overlap = !g_prof_on.load(std::memory_order_relaxed) && !confined;
   SAGE_CK(cudaEventRecord(s.fork, stream));
   SAGE_CK(cudaStreamWaitEvent(s.branch, s.fork, 0));
   const cudaStream_t main_stream = stream;
@@ -909,12 +959,13 @@ sage_status run_batch(Entry* e, const InvTable& tab, cudaStream_t stream) {
   sage_status st = acquire_slot(e, tab.M, stream, &s);
   if (st != SAGE_OK) return st;
   SAGE_CK(cudaStreamWaitEvent(stream, e->ready, 0));
-  if (e->pool->graphs && !g_prof_on.load(std::memory_order_relaxed)) {
+  const bool confined = sage::stream_is_confined(stream);
+  if (e->pool->graphs && !confined && !g_prof_on.load(std::memory_order_relaxed)) {
     st = capture_chain(e, *s, tab);
     if (st != SAGE_OK) return st;
     SAGE_CK(cudaGraphLaunch(s->exec, stream));
   } else {
-    st = launch_chain(e, *s, tab, stream);
+    st = launch_chain(e, *s, tab, stream, confined);
     if (st != SAGE_OK) return st;
   }
   SAGE_CK(cudaEventRecord(s->done, stream));
@@ -999,6 +1050,7 @@ sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
   P->serial_setup = c.serial_setup != 0;
   P->host_budget = c.host_cache_bytes;
   P->graphs = c.graphs != 0;
+  P->exportable = c.exportable != 0;
   size_t free_b = 0, total_b = 0;
   SAGE_CK(cudaMemGetInfo(&free_b, &total_b));
   const size_t margin = size_t(2) << 30;
@@ -1031,11 +1083,13 @@ sage_status sage_pool_create(const sage_pool_config* cfg, sage_pool* out) {
   return SAGE_OK;
 }
 
-sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
-  if (!P || !out) return fail(SAGE_ERR_INVALID, "null pool or out");
+// sage_prepare on local data sources (imp == nullptr), or on read-only items
+// mapped from the owning process (imp; see prepare_imported).  The descriptor
+// has been checked.
+static sage_status prepare_impl(sage_pool P, const sage_fn_desc* d, sage_fn* out,
+                                std::unique_ptr<sage::ImportedData> imp) {
   *out = nullptr;
-  sage_status st = check_desc(d);
-  if (st != SAGE_OK) return st;
+  sage_status st = SAGE_OK;
   auto t0 = Clock::now();
   SAGE_CK(cudaSetDevice(P->device));
   Entry* e = nullptr;
@@ -1049,6 +1103,7 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
         return fail(SAGE_ERR_INVALID, "key '%s' is resident with another shape", d->fn_key);
       it->second->refs++;
       P->st.hits++;
+      imp.reset();  // this process already holds the key: the extra mapping goes back
       sage_fn f = new sage_fn_s{P, it->second, kFnMagic};
       P->handles.insert(f);
       *out = f;
@@ -1070,7 +1125,8 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     e->tdesc = d->tables;
     e->wdesc = d->weights;
     e->sig = shape_sig(d);
-    {
+    e->imp = std::move(imp);
+    if (!e->imp) {
       auto hc = P->hcache.find(e->key);
       if (hc != P->hcache.end() && hc->second.sig == e->sig) {
         // re-stage from the host image (stage 2 -> resident): no producer call
@@ -1103,7 +1159,9 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     const int nslots = d->workspace_slots > 0 ? d->workspace_slots : 2;
     e->slots.resize(nslots);
     e->ws_bytes = static_cast<size_t>(nslots) * slot_bytes(e, e->max_batch);
-    const size_t need = align256(e->tables_bytes) + align256(e->weights_bytes) + e->ws_bytes + e->wsplit_bytes + 256;
+    // an imported copy is the owner's memory: only this process's workspace counts here
+    const size_t ro = e->imp ? 0 : align256(e->tables_bytes) + align256(e->weights_bytes);
+    const size_t need = ro + e->ws_bytes + e->wsplit_bytes + 256;
     if (P->used + need > P->budget) {
       delete e;
       return fail(SAGE_ERR_NOMEM, "prepare of '%s' needs %zu bytes; %zu of %zu in use", d->fn_key, need, P->used,
@@ -1142,8 +1200,13 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     e->ready = nullptr;
     return setup_failed(fail(SAGE_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(ce)));
   }
-  e->d_tables = static_cast<char*>(P->dev_alloc(e->tables_bytes, P->alloc));
-  e->d_weights = static_cast<char*>(P->dev_alloc(e->weights_bytes, P->alloc));
+  if (e->imp) {
+    e->d_tables = e->imp->tables;
+    e->d_weights = e->imp->weights;
+  } else {
+    e->d_tables = static_cast<char*>(P->ro_alloc(e->tables_bytes, P->alloc));
+    e->d_weights = static_cast<char*>(P->ro_alloc(e->weights_bytes, P->alloc));
+  }
   if (!e->d_tables || !e->d_weights)
     return setup_failed(fail(SAGE_ERR_NOMEM, "device allocation of the read-only data of '%s' failed", d->fn_key));
   if (e->wsplit_bytes) {
@@ -1195,13 +1258,23 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
   }
   {
     std::lock_guard<std::mutex> g(e->smu);
-    e->queued = true;
+    e->queued = true;  // the read-only items exist from here on
+    e->scv.notify_all();
   }
-  {
-    std::lock_guard<std::mutex> g(P->qmu);
-    P->queue.push_back(e);
+  if (e->imp) {
+    // the owner stages; this process only waits for its word, then opens the gate
+    e->imp_waiter = std::thread([P, e] {
+      cudaSetDevice(P->device);
+      const bool ok = e->imp->wait_ready();
+      finish_staging(P, e, ok, 0.0);
+    });
+  } else {
+    {
+      std::lock_guard<std::mutex> g(P->qmu);
+      P->queue.push_back(e);
+    }
+    P->qcv.notify_one();
   }
-  P->qcv.notify_one();
   if (P->serial_setup) {
     std::unique_lock<std::mutex> l(e->smu);
     e->scv.wait(l, [&] { return e->sstate != 0; });
@@ -1224,7 +1297,16 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
     ce = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming);
-    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) {
+      // SAGE_BRANCH_PRIORITY=high gives the bottom-MLP branch the highest stream
+      // priority (a tuning knob: its blocks are then scheduled ahead of the gather's)
+      int least = 0, greatest = 0;
+      const char* pr = getenv("SAGE_BRANCH_PRIORITY");
+      if (pr && strcmp(pr, "high") == 0 && cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess)
+        ce = cudaStreamCreateWithPriority(&s.branch, cudaStreamNonBlocking, greatest);
+      else
+        ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
+    }
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.h2d, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming);
@@ -1251,6 +1333,14 @@ sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
   return SAGE_OK;
 }
 
+sage_status sage_prepare(sage_pool P, const sage_fn_desc* d, sage_fn* out) {
+  if (!P || !out) return fail(SAGE_ERR_INVALID, "null pool or out");
+  *out = nullptr;
+  sage_status st = check_desc(d);
+  if (st != SAGE_OK) return st;
+  return prepare_impl(P, d, out, nullptr);
+}
+
 sage_status sage_fn_data(sage_fn f, const void** tables, const void** weights) {
   if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
   if (tables) *tables = f->e->d_tables;
@@ -1263,6 +1353,7 @@ sage_status sage_fn_query(sage_fn f) {
   Entry* e = f->e;
   std::unique_lock<std::mutex> l(e->smu);
   if (e->sstate == 2) return fail(SAGE_ERR_STAGING, "staging of '%s' failed", e->key.c_str());
+  if (e->setup == 2) return fail(SAGE_ERR_CUDA, "setup of '%s' failed", e->key.c_str());
   if (e->sstate == 0 || e->setup == 0) return SAGE_PENDING;
   cudaEvent_t ev = e->ready;
   l.unlock();
@@ -1336,6 +1427,48 @@ sage_status sage_invoke(sage_fn f, const sage_invocation* inv, void* stream) {
 }
 
 }  // extern "C"
+
+namespace sage {
+
+sage_status check_shape(const sage_fn_desc* d) { return check_shape_impl(d); }
+
+int pool_device(sage_pool P) { return P ? P->device : 0; }
+
+bool pool_exportable(sage_pool P) { return P && P->exportable; }
+
+std::string shape_signature(const sage_fn_desc* d) { return shape_sig(d); }
+
+sage_status prepare_imported(sage_pool P, const sage_fn_desc* d, ImportedData* imp, sage_fn* out) {
+  std::unique_ptr<ImportedData> own(imp);
+  if (!P || !out || !imp) return fail(SAGE_ERR_INVALID, "null pool, out or import");
+  *out = nullptr;
+  sage_status st = check_shape_impl(d);
+  if (st != SAGE_OK) return st;
+  return prepare_impl(P, d, out, std::move(own));
+}
+
+sage_status fn_export(sage_fn f, VmmBlock* tables, VmmBlock* weights) {
+  if (!valid_fn(f) || !tables || !weights) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  sage_pool_s* P = f->pool;
+  if (!P->exportable) return fail(SAGE_ERR_INVALID, "the pool was not created exportable");
+  Entry* e = f->e;
+  {
+    // a handle shared from a concurrent first prepare may precede the allocation
+    std::unique_lock<std::mutex> l(e->smu);
+    e->scv.wait(l, [&] { return e->queued || e->sstate == 2 || e->setup == 2; });
+    if (!e->queued) return fail(SAGE_ERR_STAGING, "setup of '%s' failed", e->key.c_str());
+  }
+  std::lock_guard<std::mutex> g(P->mu);
+  auto t = P->vmm.find(f->e->d_tables);
+  auto w = P->vmm.find(f->e->d_weights);
+  if (t == P->vmm.end() || w == P->vmm.end()) return fail(SAGE_ERR_INVALID, "read-only data is not exportable");
+  *tables = t->second;
+  *weights = w->second;
+  return SAGE_OK;
+}
+
+}  // namespace sage
+
 
 // Fused batch from host buffers, asynchronous on `stream`: merged H2D copies of
 // the inputs into the slot's I/O arena, the launch chain, merged D2H copies of the
@@ -1439,7 +1572,7 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
     SAGE_CK(cudaEventRecord(sl->copied, sl->h2d));
     SAGE_CK(cudaStreamWaitEvent(s, sl->copied, 0));
     SAGE_CK(cudaStreamWaitEvent(s, e->ready, 0));
-    st = launch_chain(e, *sl, *tab, s);
+    st = launch_chain(e, *sl, *tab, s, sage::stream_is_confined(s));
     if (st != SAGE_OK) return st;
     // D2H of the outputs, merged where the host outputs are adjacent
     runs.clear();

@@ -12,12 +12,15 @@
 // and the lanes of different functions overlap on the device.  A resident
 // function with nothing queued or in flight keeps its data for `linger_s`
 // (the first stage of the paper's multi-stage exit, Sec. 5.3) and is then
-// released.
+// released.  With sm_partition each function's lanes are streams of its own SM
+// partition (a green context holding SMs / n_fns SMs), so that one function's
+// batches never occupy another's SMs.
 #include <stdio.h>
 
 #include <algorithm>
 #include <chrono>
 #include <deque>
+#include <memory>
 #include <thread>
 #include <vector>
 
@@ -72,15 +75,29 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
       return sage::set_last_error("request with a bad function index or batch"), SAGE_ERR_INVALID;
     results[i] = sage_request_result{-1.0, -1.0, -1.0, 0, 0, SAGE_PENDING};
   }
+  std::unique_ptr<sage::Partition> part;
+  if (cfg.sm_partition) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    sage::Partition* p = nullptr;
+    const sage_status ps = sage::Partition::create(dev, n_fns, 0, &p);
+    if (ps != SAGE_OK) return ps;
+    part.reset(p);
+  }
   std::vector<FnState> F(n_fns);
   for (int f = 0; f < n_fns; ++f) {
     F[f].desc = fns[f];
     F[f].desc.workspace_slots = std::max(lanes, fns[f].workspace_slots);
     F[f].lanes.resize(lanes);
     for (auto& L : F[f].lanes) {
-      if (cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess)
-        return sage::set_last_error("stream/event creation failed"), SAGE_ERR_CUDA;
+      if (part) {
+        const sage_status ps = part->stream(f, &L.s);  // owned (and destroyed) by the partition
+        if (ps != SAGE_OK) return ps;
+      } else if (cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking) != cudaSuccess) {
+        return sage::set_last_error("stream creation failed"), SAGE_ERR_CUDA;
+      }
+      if (cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) != cudaSuccess)
+        return sage::set_last_error("event creation failed"), SAGE_ERR_CUDA;
     }
   }
   std::vector<int> order(n);
@@ -250,7 +267,7 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
     for (auto& L : S.lanes) {
       if (L.busy) cudaEventSynchronize(L.ev);
       cudaEventDestroy(L.ev);
-      cudaStreamDestroy(L.s);
+      if (!part) cudaStreamDestroy(L.s);
     }
     if (S.h) sage_release(S.h);
   }

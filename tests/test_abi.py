@@ -59,9 +59,10 @@ def test_ctypes_struct_sizes_match_the_header():
 #include <stddef.h>
 #include "sage.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(sage_pool_config), sizeof(sage_data_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(sage_pool_config), sizeof(sage_data_desc),
          sizeof(sage_fn_desc), sizeof(sage_invocation), sizeof(sage_host_invocation), sizeof(sage_pool_stats),
-         offsetof(sage_fn_desc, weights), sizeof(sage_kernel_time));
+         offsetof(sage_fn_desc, weights), sizeof(sage_kernel_time), sizeof(sage_share_stats),
+         offsetof(sage_pool_config, exportable), sizeof(sage_serve_config));
   return 0;
 }
 '''
@@ -72,7 +73,8 @@ int main(void) {
     got = [int(x) for x in subprocess.check_output([tmp]).split()]
     want = [ctypes.sizeof(N.PoolConfig), ctypes.sizeof(N.DataDesc), ctypes.sizeof(N.FnDesc),
             ctypes.sizeof(N.Invocation), ctypes.sizeof(N.HostInvocation), ctypes.sizeof(N.PoolStats),
-            N.FnDesc.weights.offset, ctypes.sizeof(N.KernelTime)]
+            N.FnDesc.weights.offset, ctypes.sizeof(N.KernelTime), ctypes.sizeof(N.ShareStats),
+            N.PoolConfig.exportable.offset, ctypes.sizeof(N.ServeConfig)]
     assert got == want
     os.remove(tmp)
     os.remove(tmp + ".c")
