@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
                                                            const float* __restrict__ bias, void* __restrict__ y,
                                                            int ldy, float* __restrict__ y_lo) {
   constexpr int R = 32, KM = 16;
-  __shared__ float sx[R][KM];
+  __shared__ __align__(16) float sx[R][KM];  // dense rows, zero-padded to KM
   __shared__ const float* srow[R];
   const int r0 = blockIdx.x * R;
   if (threadIdx.x < R) {
@@ -253,10 +253,17 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
     }
     const float bj = bias[j];
     for (int rr = 0; rr < nrows; ++rr) {
+      // k order 0..KM-1; the padded terms (k >= K) add 0 * 0 and leave s unchanged
+      const float4* xv = reinterpret_cast<const float4*>(&sx[rr][0]);
       float s = 0.f;
 #pragma unroll
-      for (int k = 0; k < KM; ++k)
-        if (k < K) s = fmaf(sx[rr][k], w[k], s);
+      for (int q = 0; q < KM / 4; ++q) {
+        const float4 v = xv[q];  // one broadcast read of four inputs
+        s = fmaf(v.x, w[4 * q], s);
+        s = fmaf(v.y, w[4 * q + 1], s);
+        s = fmaf(v.z, w[4 * q + 2], s);
+        s = fmaf(v.w, w[4 * q + 3], s);
+      }
       s = fmaxf(s + bj, 0.f);
       const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
       if (BF16) {

@@ -1297,16 +1297,7 @@ static sage_status prepare_impl(sage_pool P, const sage_fn_desc* d, sage_fn* out
     ce = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming);
-    if (ce == cudaSuccess) {
-      // SAGE_BRANCH_PRIORITY=high gives the bottom-MLP branch the highest stream
-      // priority (a tuning knob: its blocks are then scheduled ahead of the gather's)
-      int least = 0, greatest = 0;
-      const char* pr = getenv("SAGE_BRANCH_PRIORITY");
-      if (pr && strcmp(pr, "high") == 0 && cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess)
-        ce = cudaStreamCreateWithPriority(&s.branch, cudaStreamNonBlocking, greatest);
-      else
-        ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
-    }
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.h2d, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&s.capture, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&s.copied, cudaEventDisableTiming);
