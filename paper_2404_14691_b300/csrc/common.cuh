@@ -44,6 +44,55 @@ __device__ __forceinline__ int find_inv(const InvTable& tab, int r) {
   return lo;
 }
 
+// ---------------------------------------------------------------- head order
+//
+// The sigmoid head z = h . w + c is summed in one fixed order, shared by the head
+// kernel and by the GEMM epilogue that fuses it, so both give the same bits:
+// products h_k w_k in 32-column chunks (zero beyond K) are added by a butterfly
+// tree (pairs 16 apart, then 8, 4, 2, 1 -- what an xor-shuffle reduction gives in
+// every lane); a 64-column group is chunk(2g) + chunk(2g+1); z = g_0 + g_1 + ...
+// left to right, then + c.  Products and sums use __fmul_rn / __fadd_rn, which the
+// compiler never contracts into FMAs, so both implementations round alike.
+__device__ __forceinline__ float head_tree32(float (&p)[32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < o; ++i) p[i] = __fadd_rn(p[i], p[i + o]);
+  return p[0];
+}
+
+__device__ __forceinline__ float head_sigmoid(float z) { return 1.0f / (1.0f + expf(-z)); }
+
+// The head fused into the epilogue of the last hidden layer (N outputs, N / 64 a
+// power of two).  Each epilogue thread owns one row of a tile: it writes the row's
+// 64-column group sums to part, then adds its group count to the row's arrival
+// counter; the thread that completes the row's count (counters only grow, so
+// "complete" is modulo N / 64) sums the groups and writes the sigmoid output.
+struct HeadFuse {
+  const void* w = nullptr;    // [N] head weights, the layer's dtype
+  const float* c = nullptr;   // [1] head bias
+  float* part = nullptr;      // [rows, N / 64] group sums
+  unsigned* cnt = nullptr;    // [rows] arrival counters
+};
+struct HeadParams {
+  HeadFuse f;
+  InvTable tab;
+};
+
+// One row's part of the fused head after its group sums are stored: arrive, and
+// finish the row if this tile completes it.
+__device__ __forceinline__ void head_arrive(const HeadParams& hp, int row, unsigned add, unsigned G) {
+  __threadfence();  // the group sums before the arrival
+  const unsigned prev = atomicAdd(hp.f.cnt + row, add);
+  if ((prev + add) % G != 0) return;
+  __threadfence();  // the other tiles' group sums after their arrivals
+  const float* pr = hp.f.part + static_cast<size_t>(row) * G;
+  float z = __ldcg(pr);
+  for (unsigned g = 1; g < G; ++g) z = __fadd_rn(z, __ldcg(pr + g));
+  const int i = hp.tab.n == 1 ? 0 : find_inv(hp.tab, row);
+  hp.tab.d[i].out[row - hp.tab.d[i].row_base] = head_sigmoid(__fadd_rn(z, hp.f.c[0]));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);

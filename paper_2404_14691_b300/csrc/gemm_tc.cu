@@ -137,11 +137,13 @@ __global__ void __launch_bounds__(128, 1)
 // accumulators alternate so the epilogue of tile i overlaps the MMAs of tile i+1;
 // the shared-memory ring runs on across tiles.  warp 0 lane 0: TMA; warp 1 lane 0:
 // MMA; warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
-template <int BN, int NST>
-__global__ void __launch_bounds__(192, 1)
-    gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                              int M, int N, int K, const float* __restrict__ bias, int relu,
-                              __nv_bfloat16* __restrict__ Y, int ldy, int* err) {
+// With HEAD the epilogue writes no Y: it fuses the sigmoid head (HeadParams) on
+// the bf16-rounded activations, the values the separate head kernel would read.
+template <int BN, int NST, bool HEAD>
+__device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const CUtensorMap& tmB, int M, int N,
+                                                   int K, const float* __restrict__ bias, int relu,
+                                                   __nv_bfloat16* __restrict__ Y, int ldy, int* err,
+                                                   const HeadParams* hp) {
   using C = TcCfg<BN, NST>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -237,6 +239,37 @@ __global__ void __launch_bounds__(192, 1)
       if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
       tc_fence_after();
       const int row = m0 + q * 32 + lane;
+      if constexpr (HEAD) {
+        const unsigned G = static_cast<unsigned>(N / 64);
+        const __nv_bfloat16* hw = static_cast<const __nv_bfloat16*>(hp->f.w) + n0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 64) {
+          float gsum = 0.f;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            uint32_t v[32];
+            tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0 +
+                               32 * half,
+                           v);
+            tmem_ld_wait();
+            float p[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float o = __uint_as_float(v[j]) + __ldg(bias + n0 + c0 + 32 * half + j);
+              if (relu) o = fmaxf(o, 0.f);
+              const float ob = __bfloat162float(__float2bfloat16_rn(o));
+              p[j] = __fmul_rn(ob, __bfloat162float(hw[c0 + 32 * half + j]));
+            }
+            const float ch = head_tree32(p);
+            gsum = half == 0 ? ch : __fadd_rn(gsum, ch);
+          }
+          if (row < M) hp->f.part[static_cast<size_t>(row) * G + (n0 + c0) / 64] = gsum;
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+        if (row < M) head_arrive(*hp, row, static_cast<unsigned>(BN / 64), G);
+        continue;
+      }
       __nv_bfloat16* yrow = Y + static_cast<size_t>(row < M ? row : 0) * ldy + n0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -268,6 +301,22 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
+template <int BN, int NST>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                              int M, int N, int K, const float* __restrict__ bias, int relu,
+                              __nv_bfloat16* __restrict__ Y, int ldy, int* err) {
+  tc_persistent_body<BN, NST, false>(tmA, tmB, M, N, K, bias, relu, Y, ldy, err, nullptr);
+}
+
+template <int BN, int NST>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tc_persistent_head_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                                   int M, int N, int K, const float* __restrict__ bias, int relu, int* err,
+                                   const __grid_constant__ HeadParams hp) {
+  tc_persistent_body<BN, NST, true>(tmA, tmB, M, N, K, bias, relu, nullptr, 0, err, &hp);
 }
 
 // Row-major bf16 matrix [rows, cols] with row stride ld elements, tiles of
@@ -318,6 +367,31 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const void* x, int ldx, co
   const int grid = tiles < g_sms_pt ? tiles : g_sms_pt;
   gemm_tc_persistent_kernel<BN, NST><<<grid, 192, TcCfg<BN, NST>::SMEM, s>>>(
       ta, tb, M, N, K, bias, relu, static_cast<__nv_bfloat16*>(y), ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int BN, int NST>
+cudaError_t launch_persistent_head_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias,
+                                      int relu, int* err, cudaStream_t s, const HeadParams& hp) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_persistent_head_kernel<BN, NST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (!g_sms_pt) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_pt, cudaDevAttrMultiProcessorCount, dev);
+  }
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
+  const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
+  const int grid = tiles < g_sms_pt ? tiles : g_sms_pt;
+  gemm_tc_persistent_head_kernel<BN, NST><<<grid, 192, TcCfg<BN, NST>::SMEM, s>>>(ta, tb, M, N, K, bias, relu, err,
+                                                                                  hp);
   count_launch();
   return cudaGetLastError();
 }
@@ -385,6 +459,8 @@ void preload_tc_kernels() {
   cudaFuncGetAttributes(&fa, gemm_tc_kernel<64, 4>);
   cudaFuncGetAttributes(&fa, gemm_tc_persistent_kernel<256, 4>);
   cudaFuncGetAttributes(&fa, gemm_tc_persistent_kernel<128, 6>);
+  cudaFuncGetAttributes(&fa, gemm_tc_persistent_head_kernel<256, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tc_persistent_head_kernel<128, 6>);
   encode_fn();
 }
 
@@ -422,6 +498,20 @@ cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, c
   if (N % 256 == 0 && mt * (N / 256) >= g_sms) return launch_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return launch_bn<64, 8>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+}
+
+cudaError_t launch_linear_bf16_tc_head(int M, int N, int K, const void* x, int ldx, const void* W,
+                                       const float* bias, int relu, int* err, cudaStream_t s, GemmCfg cfg,
+                                       const HeadParams& hp) {
+  if (M <= 0) return cudaSuccess;
+  if (!head_fusable(cfg, N) || K <= 0 || (K % kBK) || (ldx % 8) || (reinterpret_cast<uintptr_t>(x) & 15) ||
+      (reinterpret_cast<uintptr_t>(W) & 15))
+    return cudaErrorInvalidValue;
+  if (cfg.bn == 256 && cfg.stages == 104)
+    return launch_persistent_head_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, err, s, hp);
+  if (cfg.bn == 128 && cfg.stages == 106)
+    return launch_persistent_head_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, err, s, hp);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace sage

@@ -313,12 +313,13 @@ __global__ void __launch_bounds__(128, 1)
 // computes tile i+1; the shared-memory ring runs on across tile boundaries.
 //   warp 0 lane 0: TMA producer; warp 1 lane 0: MMA issuer;
 //   warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
-template <int BN, int NST>
-__global__ void __launch_bounds__(192, 1)
-    gemm_tf32x3_persistent_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
-                                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
-                                  int M, int N, int K, const float* __restrict__ bias, int relu,
-                                  float* __restrict__ Yh, float* __restrict__ Yl, int ldy, int* err) {
+// With HEAD the epilogue writes no Y: it fuses the sigmoid head (HeadParams).
+template <int BN, int NST, bool HEAD>
+__device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, const CUtensorMap& tmAl,
+                                                       const CUtensorMap& tmBh, const CUtensorMap& tmBl, int M,
+                                                       int N, int K, const float* __restrict__ bias, int relu,
+                                                       float* __restrict__ Yh, float* __restrict__ Yl, int ldy,
+                                                       int* err, const HeadParams* hp) {
   using C = Tf32Cfg<BN, NST>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -424,6 +425,37 @@ __global__ void __launch_bounds__(192, 1)
       if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
       tc_fence_after();
       const int row = m0 + q * 32 + lane;
+      if constexpr (HEAD) {
+        // group sums of the head's products, then release the accumulator
+        const unsigned G = static_cast<unsigned>(N / 64);
+        const float* hw = static_cast<const float*>(hp->f.w) + n0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < BN; c0 += 64) {
+          float gsum = 0.f;
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {
+            uint32_t v[32];
+            tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0 +
+                               32 * half,
+                           v);
+            tmem_ld_wait();
+            float p[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              float o = __uint_as_float(v[j]) + __ldg(bias + n0 + c0 + 32 * half + j);
+              if (relu) o = fmaxf(o, 0.f);
+              p[j] = __fmul_rn(o, __ldg(hw + c0 + 32 * half + j));
+            }
+            const float ch = head_tree32(p);
+            gsum = half == 0 ? ch : __fadd_rn(gsum, ch);
+          }
+          if (row < M) hp->f.part[static_cast<size_t>(row) * G + (n0 + c0) / 64] = gsum;
+        }
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+        if (row < M) head_arrive(*hp, row, static_cast<unsigned>(BN / 64), G);
+        continue;
+      }
       const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -464,6 +496,26 @@ __global__ void __launch_bounds__(192, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
+template <int BN, int NST>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tf32x3_persistent_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                                  const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                                  int M, int N, int K, const float* __restrict__ bias, int relu,
+                                  float* __restrict__ Yh, float* __restrict__ Yl, int ldy, int* err) {
+  tf32x3_persistent_body<BN, NST, false>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, Yh, Yl, ldy, err, nullptr);
+}
+
+template <int BN, int NST>
+__global__ void __launch_bounds__(192, 1)
+    gemm_tf32x3_persistent_head_kernel(const __grid_constant__ CUtensorMap tmAh,
+                                       const __grid_constant__ CUtensorMap tmAl,
+                                       const __grid_constant__ CUtensorMap tmBh,
+                                       const __grid_constant__ CUtensorMap tmBl, int M, int N, int K,
+                                       const float* __restrict__ bias, int relu, int* err,
+                                       const __grid_constant__ HeadParams hp) {
+  tf32x3_persistent_body<BN, NST, true>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, nullptr, nullptr, 0, err, &hp);
 }
 
 __global__ void split_planes_kernel(const float* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo,
@@ -529,6 +581,34 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const float* xh, const flo
   return cudaGetLastError();
 }
 
+template <int BN, int NST>
+cudaError_t launch_persistent_head_bn(int M, int N, int K, const float* xh, const float* xl, int ldx,
+                                      const float* wh, const float* wl, const float* bias, int relu, int* err,
+                                      cudaStream_t s, const HeadParams& hp) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_persistent_head_kernel<BN, NST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (!g_sms_p) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_p, cudaDevAttrMultiProcessorCount, dev);
+  }
+  CUtensorMap tah, tal, tbh, tbl;
+  if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
+      !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN))
+    return cudaErrorInvalidValue;
+  const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
+  const int grid = tiles < g_sms_p ? tiles : g_sms_p;
+  gemm_tf32x3_persistent_head_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(
+      tah, tal, tbh, tbl, M, N, K, bias, relu, err, hp);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_presplit_cfg(GemmCfg c, int M, int N, int K, const float* xh, const float* xl, int ldx,
                                 const float* wh, const float* wl, const float* bias, int relu, float* yh, float* yl,
                                 int ldy, int* err, cudaStream_t s) {
@@ -589,6 +669,8 @@ void preload_tf32_kernels() {
   cudaFuncGetAttributes(&fa, gemm_tf32x3_presplit_kernel<64, 2>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_persistent_kernel<128, 3>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_persistent_kernel<64, 4>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_persistent_head_kernel<128, 3>);
+  cudaFuncGetAttributes(&fa, gemm_tf32x3_persistent_head_kernel<64, 4>);
   cudaFuncGetAttributes(&fa, split_planes_kernel);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<128, 3>);
   cudaFuncGetAttributes(&fa, gemm_tf32x3_kernel<64, 4>);
@@ -650,6 +732,21 @@ cudaError_t launch_linear_f32_tc_presplit(int M, int N, int K, const float* xh, 
   if (N % 128 == 0 && mt * (N / 128) >= g_sms)
     return launch_presplit_bn<128, 3>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
   return launch_presplit_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
+}
+
+cudaError_t launch_linear_f32_tc_presplit_head(int M, int N, int K, const float* xh, const float* xl, int ldx,
+                                               const float* wh, const float* wl, const float* bias, int relu,
+                                               int* err, cudaStream_t s, GemmCfg cfg, const HeadParams& hp) {
+  if (M <= 0) return cudaSuccess;
+  if (!head_fusable(cfg, N) || K <= 0 || (K % 4) || (ldx % 4)) return cudaErrorInvalidValue;
+  for (const void* p : {static_cast<const void*>(xh), static_cast<const void*>(xl), static_cast<const void*>(wh),
+                        static_cast<const void*>(wl)})
+    if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
+  if (cfg.bn == 128 && cfg.stages == 103)
+    return launch_persistent_head_bn<128, 3>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, err, s, hp);
+  if (cfg.bn == 64 && cfg.stages == 104)
+    return launch_persistent_head_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, err, s, hp);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s) {

@@ -80,6 +80,19 @@ cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, c
 cudaError_t launch_linear_f32_tc_presplit(int M, int N, int K, const float* xh, const float* xl, int ldx,
                                           const float* wh, const float* wl, const float* bias, int relu, float* yh,
                                           float* yl, int ldy, int* err, cudaStream_t s, GemmCfg cfg = GemmCfg{0, 0});
+// True when the last hidden layer (N outputs) can fuse the sigmoid head with tile
+// configuration cfg: a persistent configuration and N / 64 a power of two.
+inline bool head_fusable(GemmCfg cfg, int N) {
+  const int G = N / 64;
+  return cfg.stages >= 100 && cfg.bn > 0 && N % 64 == 0 && N % cfg.bn == 0 && G > 0 && (G & (G - 1)) == 0;
+}
+// The last hidden layer with the head fused (hp); writes no Y.
+cudaError_t launch_linear_f32_tc_presplit_head(int M, int N, int K, const float* xh, const float* xl, int ldx,
+                                               const float* wh, const float* wl, const float* bias, int relu,
+                                               int* err, cudaStream_t s, GemmCfg cfg, const HeadParams& hp);
+cudaError_t launch_linear_bf16_tc_head(int M, int N, int K, const void* x, int ldx, const void* W,
+                                       const float* bias, int relu, int* err, cudaStream_t s, GemmCfg cfg,
+                                       const HeadParams& hp);
 // hi[i] = tf32(src[i]) (round to nearest), lo[i] = src[i] - hi[i].
 cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s);
 // fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.

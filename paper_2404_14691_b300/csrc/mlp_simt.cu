@@ -280,38 +280,44 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
 }
 
 // ---------------------------------------------------------------- head
-// One warp per batch row: z = h . w + c (lane partial sums over k = lane, lane+32,
-// ..., then a fixed xor tree), out = 1 / (1 + exp(-z)) written to the row's
-// invocation.
+// One warp per batch row: z = h . w + c in the fixed head order (a 32-column
+// chunk per load, lane j holding column k0 + j, summed by xor shuffles), out =
+// 1 / (1 + exp(-z)) written to the row's invocation.
 template <bool BF16>
 __global__ void __launch_bounds__(256) head_kernel(const __grid_constant__ InvTable tab, int K,
                                                   const void* __restrict__ h, int ldh, const void* __restrict__ w,
                                                   const float* __restrict__ c, const float* __restrict__ h_lo) {
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < tab.M; r += warps) {
-    float s = 0.f;
-    if (BF16) {
-      const __nv_bfloat16* hr = reinterpret_cast<const __nv_bfloat16*>(h) + static_cast<size_t>(r) * ldh;
-      const __nv_bfloat16* ww = reinterpret_cast<const __nv_bfloat16*>(w);
-      for (int k = lane; k < K; k += 32) s = fmaf(__bfloat162float(hr[k]), __bfloat162float(ww[k]), s);
-    } else {
-      const float* hr = reinterpret_cast<const float*>(h) + static_cast<size_t>(r) * ldh;
-      const float* ww = reinterpret_cast<const float*>(w);
-      if (h_lo) {
-        // hi + lo planes: the sum is the fp32 value exactly (lo is the exact residual)
-        const float* lr = h_lo + static_cast<size_t>(r) * ldh;
-        for (int k = lane; k < K; k += 32) s = fmaf(hr[k] + lr[k], ww[k], s);
+  auto chunk = [&](int r, int k0) {
+    const int k = k0 + lane;
+    float p = 0.f;
+    if (k < K) {
+      float hv, wv;
+      if (BF16) {
+        hv = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(h)[static_cast<size_t>(r) * ldh + k]);
+        wv = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(w)[k]);
       } else {
-        for (int k = lane; k < K; k += 32) s = fmaf(hr[k], ww[k], s);
+        const size_t o = static_cast<size_t>(r) * ldh + k;
+        // hi + lo planes: the sum is the fp32 value exactly (lo is the exact residual)
+        hv = h_lo ? __fadd_rn(reinterpret_cast<const float*>(h)[o], h_lo[o]) : reinterpret_cast<const float*>(h)[o];
+        wv = reinterpret_cast<const float*>(w)[k];
       }
+      p = __fmul_rn(hv, wv);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = 16; o > 0; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+    return p;
+  };
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < tab.M; r += warps) {
+    float z = 0.f;
+    for (int k0 = 0; k0 < K; k0 += 64) {
+      const float g = __fadd_rn(chunk(r, k0), chunk(r, k0 + 32));
+      z = k0 == 0 ? g : __fadd_rn(z, g);
+    }
     if (lane == 0) {
       const int i = tab.n == 1 ? 0 : find_inv(tab, r);
-      const float z = s + c[0];
-      tab.d[i].out[r - tab.d[i].row_base] = 1.0f / (1.0f + expf(-z));
+      tab.d[i].out[r - tab.d[i].row_base] = head_sigmoid(__fadd_rn(z, c[0]));
     }
   }
 }

@@ -185,6 +185,9 @@ struct Slot {
   std::vector<char*> bot;  // bottom hidden outputs except the last layer's
   char* concat = nullptr;
   std::vector<char*> top;  // top hidden outputs except the head's
+  // head fused into the last hidden layer: per-row group sums and arrival counters
+  float* hpart = nullptr;
+  unsigned* hcnt = nullptr;
   char* io = nullptr;
   size_t io_bytes = 0;
   cudaEvent_t done = nullptr;
@@ -551,6 +554,16 @@ double load_kernels_once() {
 // planes per activation buffer: 2 (hi, lo) for pre-split fp32 functions
 size_t planes(const Entry* e) { return e->presplit ? 2 : 1; }
 
+// Groups of 64 columns of the last hidden top layer when the head can be fused
+// into its epilogue (tensor-core layer, N / 64 a power of two), else 0.
+int head_groups(const Entry* e) {
+  if (e->top.size() < 2) return 0;
+  const int N = e->top[e->top.size() - 2];
+  const int G = N / 64;
+  if (N % 64 || G < 1 || (G & (G - 1))) return 0;
+  return (e->dtype == SAGE_BF16 || e->presplit) ? G : 0;
+}
+
 size_t slot_bytes(const Entry* e, int cap) {
   size_t b = 0;
   const size_t pl = planes(e);
@@ -559,6 +572,7 @@ size_t slot_bytes(const Entry* e, int cap) {
   b += align256(pl * static_cast<size_t>(cap) * e->concat_dim() * e->elem());
   for (size_t l = 0; l + 1 < e->top.size(); ++l)
     b += align256(pl * static_cast<size_t>(cap) * e->top[l] * e->elem());
+  if (const int G = head_groups(e)) b += align256(static_cast<size_t>(cap) * G * 4) + align256(static_cast<size_t>(cap) * 4);
   return b;
 }
 
@@ -584,6 +598,15 @@ sage_status build_slot(Entry* e, Slot& s, int cap, cudaStream_t stream) {
   for (size_t l = 0; l + 1 < e->top.size(); ++l) {
     s.top.push_back(buf + o);
     o += align256(pl * static_cast<size_t>(cap) * e->top[l] * e->elem());
+  }
+  s.hpart = nullptr;
+  s.hcnt = nullptr;
+  if (const int G = head_groups(e)) {
+    s.hpart = reinterpret_cast<float*>(buf + o);
+    o += align256(static_cast<size_t>(cap) * G * 4);
+    s.hcnt = reinterpret_cast<unsigned*>(buf + o);
+    o += align256(static_cast<size_t>(cap) * 4);
+    SAGE_CK(cudaMemsetAsync(s.hcnt, 0, static_cast<size_t>(cap) * 4, stream));
   }
   return SAGE_OK;
 }
@@ -870,9 +893,32 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   // top MLP hidden layers
   const char* x = s.concat;
   int ldx = cd;
+  const Layer& H = e->layers[nb + nt - 1];
   for (int l = 0; l + 1 < nt; ++l) {
     const Layer& L = e->layers[nb + l];
     char* y = s.top[l];
+    if (l + 2 == nt && s.hcnt) {
+      // the last hidden layer with the sigmoid head in its epilogue (when its tuned
+      // tile configuration is a persistent one)
+      const GemmCfg c = tuned_gemm(e->dtype == SAGE_BF16 ? kGemmBf16 : kGemmTf32Pre, M, L.out, L.in);
+      if (head_fusable(c, L.out)) {
+        HeadParams hp;
+        hp.f.w = H.W;
+        hp.f.c = H.b;
+        hp.f.part = s.hpart;
+        hp.f.cnt = s.hcnt;
+        hp.tab = tab;
+        ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : kProfGemmTf32,
+                     2.0 * M * L.in * L.out + 2.0 * M * H.in);
+        if (e->dtype == SAGE_BF16)
+          SAGE_CK(launch_linear_bf16_tc_head(M, L.out, L.in, x, ldx, L.W, L.b, 1, e->d_err, stream, c, hp));
+        else
+          SAGE_CK(launch_linear_f32_tc_presplit_head(M, L.out, L.in, reinterpret_cast<const float*>(x),
+                                                     lo_of(x, ldx), ldx, e->wplanes[nb + l].first,
+                                                     e->wplanes[nb + l].second, L.b, 1, e->d_err, stream, c, hp));
+        return SAGE_OK;
+      }
+    }
     ProfScope ps(stream, e->dtype == SAGE_BF16 ? kProfGemmTc : f32_kind(L.out, L.in, ldx, L.out),
                  2.0 * M * L.in * L.out);
     if (e->dtype == SAGE_BF16)
@@ -888,7 +934,6 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     ldx = L.out;
   }
   // sigmoid head, written to each invocation's out
-  const Layer& H = e->layers[nb + nt - 1];
   ProfScope ps(stream, kProfHead, 2.0 * M * H.in);
   SAGE_CK(launch_head(e->dtype, tab, H.in, x, ldx, H.W, H.b, stream, lo_of(x, ldx)));
   return SAGE_OK;
@@ -1651,6 +1696,12 @@ sage_status sage_fn_check(sage_fn f) {
   int w = 0;
   SAGE_CK(cudaMemcpy(&w, e->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   SAGE_CK(cudaMemset(e->d_err, 0, sizeof(int)));
+  if (w & kErrTimeout) {
+    // a kernel that gave up may have left fused-head arrival counters short
+    std::lock_guard<std::mutex> g(e->imu);
+    for (auto& s : e->slots)
+      if (s.hcnt) SAGE_CK(cudaMemset(s.hcnt, 0, static_cast<size_t>(s.cap) * 4));
+  }
   if (w & kErrTimeout) return fail(SAGE_ERR_DEVICE, "a kernel's bounded wait ran out");
   if (w & kErrBounds) return fail(SAGE_ERR_BOUNDS, "a bag row index was outside its table");
   return SAGE_OK;

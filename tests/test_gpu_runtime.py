@@ -425,6 +425,40 @@ def test_fp32_presplit_tile_configurations_bitwise(pool, tile):
         f.release()
 
 
+@pytest.mark.parametrize("tile", [(128, 106), (64, 8), (128, 3)])
+def test_bf16_head_fused_or_separate_bitwise(pool, tile):
+    """The sigmoid head fused into the last hidden layer's epilogue (persistent tiles)
+    gives the bits of the separate head kernel (other tiles), and matches the oracle."""
+    torch = _torch()
+    spec = workload.FunctionSpec(key="rt_head_%d_%d" % tile, dtype="bf16", rows=[4000, 3000, 5000], dim=64,
+                                 bot_dims=[128, 64], top_dims=[256, 128, 1], alpha=1.1, l_min=0, l_max=40)
+    f = prepare(pool, spec, max_batch=3000)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=700 + i) for i, B in enumerate([900, 1100, 13, 0, 1])]
+        M = sum(v["batch"] for v in invs)
+        sage.tuning_set(1, M, 128, 256, 64, 8)          # separate head
+        ref = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in ref])
+        torch.cuda.synchronize()
+        sage.tuning_set(1, M, 128, 256, tile[0], tile[1])
+        got = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in got])
+        # the arrival counters only grow: launches of other sizes in between (rows past
+        # a smaller batch keep their counts) must not disturb the next full batch
+        f.invoke_batch([d.args() for d in got[2:]])
+        f.invoke_batch([d.args() for d in got[:1]])
+        again = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in again])
+        torch.cuda.synchronize()
+        f.check_errors()
+        for a, b, c in zip(ref, got, again):
+            assert torch.equal(a.out[:a.batch], b.out[:b.batch])
+            assert torch.equal(a.out[:a.batch], c.out[:c.batch])
+        _check_inv(spec, workload.weights_arrays(spec), got[1], RTOL["bf16"])
+    finally:
+        f.release()
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_cuda_graph_replay_equals_direct_launches(dtype):
     """Batches replayed through the captured CUDA graph (updated in place between batches
