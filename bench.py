@@ -485,14 +485,17 @@ def h2d_link_gbs(torch, nbytes=1 << 30):
     return round(best, 1)
 
 
-def make_trace(specs, n, rate, per_fn_invs, seed, burst=False):
-    """Requests over the functions: Poisson arrivals (or all at t=0), uniform function choice,
-    each request reusing one of per_fn_invs pre-generated invocations of its function."""
+def make_trace(specs, n, rate, per_fn_invs, seed, burst=False, fns=None, arrivals=None):
+    """Requests over the functions: Poisson arrivals (or all at t=0), uniform function choice
+    (or the given fns / arrivals), each request reusing one of per_fn_invs pre-generated
+    invocations of its function."""
     import torch
     import paper_2404_14691_b300 as sage
     rng = np.random.default_rng(seed)
-    arrivals = np.zeros(n) if burst else np.cumsum(rng.exponential(1.0 / rate, size=n))
-    fns = rng.integers(0, len(specs), size=n)
+    if arrivals is None:
+        arrivals = np.zeros(n) if burst else np.cumsum(rng.exponential(1.0 / rate, size=n))
+    if fns is None:
+        fns = rng.integers(0, len(specs), size=n)
     pool_invs = []
     for f, spec in enumerate(specs):
         sizes = workload.batch_sizes_lognormal(per_fn_invs, seed=workload.sub_seed("serve", "sizes", f))
@@ -583,6 +586,37 @@ def run_serve(args):
             h.release()
         pool.destroy()
     same_part = bool(torch.equal(outs["warm_shared_sms"], outs["warm_sm_partition"]))
+    # interference: a heavy function (26 x 4M x 128) under a saturating stream while a light
+    # one (8 x 1M x 64) receives 200 requests/s; all SMs shared vs one SM partition each
+    sel = [specs[2], specs[0]]
+    n_h, n_l = 3000, 200
+    irng = np.random.default_rng(workload.sub_seed("serve", "interference") % (1 << 63))
+    fns_i = np.array([0] * n_h + [1] * n_l)
+    arr_i = np.concatenate([np.cumsum(irng.exponential(1.0 / 3000.0, size=n_h)),
+                            np.cumsum(irng.exponential(1.0 / 200.0, size=n_l))])
+    ireqs, iout, ikeep = make_trace(sel, n_h + n_l, 0.0, 8, seed=workload.sub_seed("serve", "itrace") % (1 << 63),
+                                    fns=fns_i, arrivals=arr_i)
+    ikw = [workload.prepare_kwargs(s) for s in sel]
+    inter, iouts = {}, {}
+    for mode, part in (("shared_sms", False), ("sm_partition", True)):
+        pool = sage.Pool(device=0)
+        held = [pool.prepare(**kw) for kw in ikw]
+        for h in held:
+            h.wait()
+        r, st = sage.serve(pool, ikw, ireqs, lanes_per_fn=2, sm_partition=part)
+        row = {"wall_s": round(st["wall_s"], 3), "completed": st["completed"]}
+        for fi, name in ((0, "heavy"), (1, "light")):
+            lat = sorted(x["latency_ms"] for x, q in zip(r, ireqs) if q[0] == fi)
+            row[name] = {"requests": len(lat), "p50_ms": round(lat[len(lat) // 2], 3),
+                         "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)}
+        row["heavy"]["invocations_per_s"] = round(n_h / max(1e-9, max(x["latency_ms"] / 1e3 + q[1] for x, q in
+                                                                    zip(r, ireqs) if q[0] == 0)), 1)
+        inter[mode] = row
+        iouts[mode] = iout.clone()
+        for h in held:
+            h.release()
+        pool.destroy()
+    inter["outputs_identical"] = bool(torch.equal(iouts["shared_sms"], iouts["sm_partition"]))
     # multi-stage exit of one function (26 x 1M x 128 bf16), the structure of the paper's
     # per-stage latency table: cold (producer), stage 1 (resident), stage 2 (host cache)
     stages = {}
@@ -635,6 +669,7 @@ def run_serve(args):
                                    "B~round(LogNormal(ln256,1)), L~U[1,100], cold start" % (n, total_ro / 1e9)},
             "served": res["served"], "plain": res["plain"], "outputs_identical": same,
             "warm_saturation": sat, "warm_poisson": warm, "partition_outputs_identical": same_part,
+            "interference": inter,
             "multi_stage": stages, "h2d_link_gbs": link, "clocks": clocks}
     return line
 

@@ -79,18 +79,38 @@ struct HeadParams {
   InvTable tab;
 };
 
-// One row's part of the fused head after its group sums are stored: arrive, and
-// finish the row if this tile completes it.
-__device__ __forceinline__ void head_arrive(const HeadParams& hp, int row, unsigned add, unsigned G) {
-  __threadfence();  // the group sums before the arrival
-  const unsigned prev = atomicAdd(hp.f.cnt + row, add);
-  if ((prev + add) % G != 0) return;
-  __threadfence();  // the other tiles' group sums after their arrivals
-  const float* pr = hp.f.part + static_cast<size_t>(row) * G;
-  float z = __ldcg(pr);
-  for (unsigned g = 1; g < G; ++g) z = __fadd_rn(z, __ldcg(pr + g));
+__device__ __forceinline__ void head_write(const HeadParams& hp, int row, float z) {
   const int i = hp.tab.n == 1 ? 0 : find_inv(hp.tab, row);
   hp.tab.d[i].out[row - hp.tab.d[i].row_base] = head_sigmoid(__fadd_rn(z, hp.f.c[0]));
+}
+
+// Finish one row of the fused head from this tile's NG group sums gs (groups
+// g0 .. g0+NG-1 of G).  A tile holding the whole row (NG == G) finishes it in
+// registers; otherwise the sums go to part and the row's counter is bumped with
+// one acquire-release atomic (it publishes these sums and, for the tile that
+// completes the row, makes the other tiles' sums visible).
+template <int NG>
+__device__ __forceinline__ void head_row(const HeadParams& hp, int row, const float (&gs)[NG], unsigned g0,
+                                         unsigned G) {
+  if (NG == G) {
+    float z = gs[0];
+#pragma unroll
+    for (int g = 1; g < NG; ++g) z = __fadd_rn(z, gs[g]);
+    head_write(hp, row, z);
+    return;
+  }
+  float* pr = hp.f.part + static_cast<size_t>(row) * G;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) pr[g0 + g] = gs[g];
+  unsigned prev;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], %2;"
+               : "=r"(prev)
+               : "l"(hp.f.cnt + row), "r"(static_cast<unsigned>(NG))
+               : "memory");
+  if ((prev + NG) % G != 0) return;
+  float z = __ldcg(pr);
+  for (unsigned g = 1; g < G; ++g) z = __fadd_rn(z, __ldcg(pr + g));
+  head_write(hp, row, z);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {

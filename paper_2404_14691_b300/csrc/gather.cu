@@ -9,6 +9,8 @@
 // order; the RPW partial sums are then combined by a fixed xor tree.  The order
 // of every sum therefore depends only on the bag itself, never on the batch it
 // runs in, which makes fused and isolated invocations bitwise identical.
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace sage {
@@ -50,47 +52,56 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
 
-    for (int64_t j0 = beg; j0 < end; j0 += 32) {
-      const int cnt = static_cast<int>(min(static_cast<int64_t>(32), end - j0));
-      const int my = lane < cnt ? __ldg(d.indices + j0 + lane) : 0;
-      for (int q = 0; q < cnt; q += RPW * U) {
-        uint4 v[U][VPL];
-        bool ok[U];
+    // one step: UU row loads in flight per lane, positions q + u*RPW + sub; the
+    // position check is needed only in a bag's last, partial steps
+    auto step = [&](int q, int cnt, int my, auto uu, auto checked) {
+      constexpr int UU = decltype(uu)::value;
+      uint4 v[UU][VPL];
+      bool ok[UU];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int p = q + u * RPW + sub;
-          const int row = __shfl_sync(0xffffffffu, my, p & 31);
-          ok[u] = p < cnt;
-          if (ok[u] && static_cast<unsigned>(row) >= rows) {
-            ok[u] = false;
-            if (a.err) atomicOr(a.err, kErrBounds);
-          }
-          const uint4* src = reinterpret_cast<const uint4*>(base + static_cast<size_t>(ok[u] ? row : 0) * row_bytes) + col;
-#pragma unroll
-          for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w * LPR) : make_uint4(0, 0, 0, 0);
+      for (int u = 0; u < UU; ++u) {
+        const int p = q + u * RPW + sub;
+        const int row = __shfl_sync(0xffffffffu, my, p & 31);
+        ok[u] = decltype(checked)::value ? p < cnt : true;
+        if (ok[u] && static_cast<unsigned>(row) >= rows) {
+          ok[u] = false;
+          if (a.err) atomicOr(a.err, kErrBounds);
         }
+        const uint4* src = reinterpret_cast<const uint4*>(base + static_cast<size_t>(ok[u] ? row : 0) * row_bytes) + col;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (!ok[u]) continue;
+        for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w * LPR) : make_uint4(0, 0, 0, 0);
+      }
 #pragma unroll
-          for (int w = 0; w < VPL; ++w) {
-            if (BF16) {
-              const uint32_t wd[4] = {v[u][w].x, v[u][w].y, v[u][w].z, v[u][w].w};
+      for (int u = 0; u < UU; ++u) {
+        if (!ok[u]) continue;
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float2 f = unpack_bf16x2(wd[e]);
-                acc[w][2 * e] += f.x;
-                acc[w][2 * e + 1] += f.y;
-              }
-            } else {
-              acc[w][0] += __uint_as_float(v[u][w].x);
-              acc[w][1] += __uint_as_float(v[u][w].y);
-              acc[w][2] += __uint_as_float(v[u][w].z);
-              acc[w][3] += __uint_as_float(v[u][w].w);
+        for (int w = 0; w < VPL; ++w) {
+          if (BF16) {
+            const uint32_t wd[4] = {v[u][w].x, v[u][w].y, v[u][w].z, v[u][w].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float2 f = unpack_bf16x2(wd[e]);
+              acc[w][2 * e] += f.x;
+              acc[w][2 * e + 1] += f.y;
             }
+          } else {
+            acc[w][0] += __uint_as_float(v[u][w].x);
+            acc[w][1] += __uint_as_float(v[u][w].y);
+            acc[w][2] += __uint_as_float(v[u][w].z);
+            acc[w][3] += __uint_as_float(v[u][w].w);
           }
         }
       }
+    };
+    constexpr int UT = U < 2 ? U : 2;  // tail: fewer loads per step, fewer idle slots
+    for (int64_t j0 = beg; j0 < end; j0 += 32) {
+      const int cnt = static_cast<int>(min(static_cast<int64_t>(32), end - j0));
+      const int my = lane < cnt ? __ldg(d.indices + j0 + lane) : 0;
+      int q = 0;
+      // each lane still adds its positions in increasing order: same sums as one loop
+      for (; q + RPW * U <= cnt; q += RPW * U)
+        step(q, cnt, my, std::integral_constant<int, U>(), std::false_type());
+      for (; q < cnt; q += RPW * UT) step(q, cnt, my, std::integral_constant<int, UT>(), std::true_type());
     }
     // combine the RPW sub-group partial sums (fixed tree; a+b == b+a exactly)
 #pragma unroll

@@ -429,7 +429,8 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
         // group sums of the head's products, then release the accumulator
         const unsigned G = static_cast<unsigned>(N / 64);
         const float* hw = static_cast<const float*>(hp->f.w) + n0;
-#pragma unroll 1
+        float gs[BN / 64];
+#pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 64) {
           float gsum = 0.f;
 #pragma unroll
@@ -449,11 +450,11 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
             const float ch = head_tree32(p);
             gsum = half == 0 ? ch : __fadd_rn(gsum, ch);
           }
-          if (row < M) hp->f.part[static_cast<size_t>(row) * G + (n0 + c0) / 64] = gsum;
+          gs[c0 / 64] = gsum;
         }
         tc_fence_before();
         mbar_arrive(&acc_empty[buf]);
-        if (row < M) head_arrive(*hp, row, static_cast<unsigned>(BN / 64), G);
+        if (row < M) head_row<BN / 64>(*hp, row, gs, static_cast<unsigned>(n0 / 64), G);
         continue;
       }
       const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;

@@ -900,7 +900,15 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     if (l + 2 == nt && s.hcnt) {
       // the last hidden layer with the sigmoid head in its epilogue (when its tuned
       // tile configuration is a persistent one)
-      const GemmCfg c = tuned_gemm(e->dtype == SAGE_BF16 ? kGemmBf16 : kGemmTf32Pre, M, L.out, L.in);
+      const int kind = e->dtype == SAGE_BF16 ? kGemmBf16 : kGemmTf32Pre;
+      GemmCfg c = tuned_gemm(kind, M, L.out, L.in);
+      if (head_fusable(c, L.out) && c.bn < L.out) {
+        // a persistent tile as wide as the layer finishes each row in registers
+        GemmCfg cands[16];
+        const int nc = gemm_candidates(kind, cands, 16);
+        for (int i = 0; i < nc; ++i)
+          if (cands[i].stages >= 100 && cands[i].bn == L.out) c = cands[i];
+      }
       if (head_fusable(c, L.out)) {
         HeadParams hp;
         hp.f.w = H.W;

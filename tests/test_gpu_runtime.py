@@ -425,6 +425,38 @@ def test_fp32_presplit_tile_configurations_bitwise(pool, tile):
         f.release()
 
 
+@pytest.mark.parametrize("tile", [(128, 103), (64, 104)])
+def test_fp32_head_fused_across_tiles_bitwise(pool, tile):
+    """A last hidden layer wider than one tile (256 outputs, tiles of 128 or 64): each row's
+    head is finished by whichever tile completes it (group sums + arrival counters), with the
+    bits of the separate head kernel."""
+    torch = _torch()
+    spec = workload.spec_tiny(key="rt_hx_%d" % tile[0], dtype="f32", n_tables=3, rows=3000, dim=32,
+                              bot=(64, 32), top=(128, 256, 1), l_min=0, l_max=30)
+    f = prepare(pool, spec, max_batch=3000)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=720 + i) for i, B in enumerate([1000, 7, 0, 1500])]
+        M = sum(v["batch"] for v in invs)
+        sage.tuning_set(3, M, 256, 128, 64, 4)          # non-persistent: separate head kernel
+        ref = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in ref])
+        torch.cuda.synchronize()
+        sage.tuning_set(3, M, 256, 128, tile[0], tile[1])
+        runs = []
+        for _ in range(3):                              # counters carry over launches
+            got = [DevInvocation(v) for v in invs]
+            f.invoke_batch([d.args() for d in got])
+            runs.append(got)
+        torch.cuda.synchronize()
+        f.check_errors()
+        for got in runs:
+            for a, b in zip(ref, got):
+                assert torch.equal(a.out[:a.batch], b.out[:b.batch])
+        _check_inv(spec, workload.weights_arrays(spec), runs[0][3], RTOL["f32"])
+    finally:
+        f.release()
+
+
 @pytest.mark.parametrize("tile", [(128, 106), (64, 8), (128, 3)])
 def test_bf16_head_fused_or_separate_bitwise(pool, tile):
     """The sigmoid head fused into the last hidden layer's epilogue (persistent tiles)
