@@ -23,6 +23,18 @@ struct Acc {
 
 __device__ __forceinline__ uint4 ldg_nc_v4(const uint4* p) { return __ldg(p); }
 
+// Two independent fp32 additions (round to nearest) in one instruction: the low
+// halves and the high halves of two 64-bit registers, as two scalar adds would.
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t pack2(uint32_t lo, uint32_t hi) {
+  return static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+}
+
 template <bool BF16, int LPR, int VPL, int U>
 __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a,
                                                      const __grid_constant__ InvTable tab) {
@@ -46,11 +58,19 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
     const char* base = a.tables + a.table_off[t];
     const unsigned rows = static_cast<unsigned>(a.table_rows[t]);
 
+    // running sums: bf16 rows as fp32 pairs added two at a time (element 2e in the low
+    // half, 2e+1 in the high half); fp32 rows one by one (repacking their 16-byte
+    // loads into pairs costs more than it saves).  Either way each element gets the
+    // same sequence of round-to-nearest fp32 additions.
+    uint64_t acc2[VPL][EPV / 2];
     float acc[VPL][EPV];
 #pragma unroll
-    for (int w = 0; w < VPL; ++w)
+    for (int w = 0; w < VPL; ++w) {
+#pragma unroll
+      for (int e = 0; e < EPV / 2; ++e) acc2[w][e] = 0;
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
+    }
 
     // one step: UU row loads in flight per lane, positions q + u*RPW + sub; the
     // position check is needed only in a bag's last, partial steps
@@ -77,13 +97,10 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
 #pragma unroll
         for (int w = 0; w < VPL; ++w) {
           if (BF16) {
+            // a bf16 is the top half of its fp32 value
             const uint32_t wd[4] = {v[u][w].x, v[u][w].y, v[u][w].z, v[u][w].w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float2 f = unpack_bf16x2(wd[e]);
-              acc[w][2 * e] += f.x;
-              acc[w][2 * e + 1] += f.y;
-            }
+            for (int e = 0; e < 4; ++e) acc2[w][e] = add_f32x2(acc2[w][e], pack2(wd[e] << 16, wd[e] & 0xffff0000u));
           } else {
             acc[w][0] += __uint_as_float(v[u][w].x);
             acc[w][1] += __uint_as_float(v[u][w].y);
@@ -102,6 +119,15 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       for (; q + RPW * U <= cnt; q += RPW * U)
         step(q, cnt, my, std::integral_constant<int, U>(), std::false_type());
       for (; q < cnt; q += RPW * UT) step(q, cnt, my, std::integral_constant<int, UT>(), std::true_type());
+    }
+    if (BF16) {
+#pragma unroll
+      for (int w = 0; w < VPL; ++w)
+#pragma unroll
+        for (int e = 0; e < EPV / 2; ++e) {
+          acc[w][2 * e] = __uint_as_float(static_cast<uint32_t>(acc2[w][e]));
+          acc[w][2 * e + 1] = __uint_as_float(static_cast<uint32_t>(acc2[w][e] >> 32));
+        }
     }
     // combine the RPW sub-group partial sums (fixed tree; a+b == b+a exactly)
 #pragma unroll
