@@ -85,6 +85,20 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
     part.reset(p);
   }
   std::vector<FnState> F(n_fns);
+  // every exit destroys the lanes' events and streams (partition streams belong to the partition)
+  struct LaneGuard {
+    std::vector<FnState>& F;
+    bool own_streams;
+    ~LaneGuard() {
+      for (auto& S : F)
+        for (auto& L : S.lanes) {
+          if (L.ev) cudaEventDestroy(L.ev);
+          if (L.s && own_streams) cudaStreamDestroy(L.s);
+          L.ev = nullptr;
+          L.s = nullptr;
+        }
+    }
+  } guard{F, !cfg.sm_partition};
   for (int f = 0; f < n_fns; ++f) {
     F[f].desc = fns[f];
     F[f].desc.workspace_slots = std::max(lanes, fns[f].workspace_slots);
@@ -266,8 +280,6 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
   for (auto& S : F) {
     for (auto& L : S.lanes) {
       if (L.busy) cudaEventSynchronize(L.ev);
-      cudaEventDestroy(L.ev);
-      if (!part) cudaStreamDestroy(L.s);
     }
     if (S.h) sage_release(S.h);
   }
