@@ -5,7 +5,7 @@ It defines *what the inputs are* -- embedding tables, MLP weights, dense
 features, bag indices/offsets, batch sizes, arrival times -- and holds none of
 the method's arithmetic (no pooling, no MLP, no packing).
 
-Recipe (the readings of the workload descriptions this build runs):
+Recipe (how the workload descriptions are read):
   * tables: uniform on [-0.05, 0.05), counter-based SplitMix64 values (gen.c);
     BF16 functions store them rounded to nearest-even.
   * weights: Xavier-uniform, bound sqrt(6/(fan_in+fan_out)); biases uniform
