@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
   }
   __syncthreads();
   const int nrows = min(R, tab.M - r0);
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    float w[KM];
+  auto load_w = [&](int j, float (&w)[KM]) {
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
       if (k < K) {
@@ -251,20 +250,57 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
         w[k] = 0.f;
       }
     }
+  };
+  // k order 0..KM-1; the padded terms (k >= K) add 0 * 0 and leave s unchanged
+  auto dot = [&](const float4 (&x)[KM / 4], const float (&w)[KM], float b) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < KM / 4; ++q) {
+      s = fmaf(x[q].x, w[4 * q], s);
+      s = fmaf(x[q].y, w[4 * q + 1], s);
+      s = fmaf(x[q].z, w[4 * q + 2], s);
+      s = fmaf(x[q].w, w[4 * q + 3], s);
+    }
+    return fmaxf(s + b, 0.f);
+  };
+  // two adjacent columns per thread (one 8-byte / bf16-pair store per row and plane)
+  // when the layout allows it, else one
+  const bool pairs = (N % 2 == 0) && (ldy % 2 == 0) && !(reinterpret_cast<uintptr_t>(y) & 7) &&
+                     !(reinterpret_cast<uintptr_t>(y_lo) & 7);
+  if (pairs) {
+    for (int j = 2 * static_cast<int>(threadIdx.x); j < N; j += 2 * blockDim.x) {
+      float w0[KM], w1[KM];
+      load_w(j, w0);
+      load_w(j + 1, w1);
+      const float b0 = bias[j], b1 = bias[j + 1];
+      for (int rr = 0; rr < nrows; ++rr) {
+        float4 x[KM / 4];
+#pragma unroll
+        for (int q = 0; q < KM / 4; ++q) x[q] = reinterpret_cast<const float4*>(&sx[rr][0])[q];  // broadcasts
+        const float s0 = dot(x, w0, b0), s1 = dot(x, w1, b1);
+        const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
+        if (BF16) {
+          *reinterpret_cast<uint32_t*>(reinterpret_cast<__nv_bfloat16*>(y) + o) = pack_bf16x2(s0, s1);
+        } else if (y_lo) {
+          const float h0 = to_tf32_rna(s0), h1 = to_tf32_rna(s1);
+          *reinterpret_cast<float2*>(reinterpret_cast<float*>(y) + o) = make_float2(h0, h1);
+          *reinterpret_cast<float2*>(y_lo + o) = make_float2(s0 - h0, s1 - h1);
+        } else {
+          *reinterpret_cast<float2*>(reinterpret_cast<float*>(y) + o) = make_float2(s0, s1);
+        }
+      }
+    }
+    return;
+  }
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float w[KM];
+    load_w(j, w);
     const float bj = bias[j];
     for (int rr = 0; rr < nrows; ++rr) {
-      // k order 0..KM-1; the padded terms (k >= K) add 0 * 0 and leave s unchanged
-      const float4* xv = reinterpret_cast<const float4*>(&sx[rr][0]);
-      float s = 0.f;
+      float4 x[KM / 4];
 #pragma unroll
-      for (int q = 0; q < KM / 4; ++q) {
-        const float4 v = xv[q];  // one broadcast read of four inputs
-        s = fmaf(v.x, w[4 * q], s);
-        s = fmaf(v.y, w[4 * q + 1], s);
-        s = fmaf(v.z, w[4 * q + 2], s);
-        s = fmaf(v.w, w[4 * q + 3], s);
-      }
-      s = fmaxf(s + bj, 0.f);
+      for (int q = 0; q < KM / 4; ++q) x[q] = reinterpret_cast<const float4*>(&sx[rr][0])[q];
+      const float s = dot(x, w, bj);
       const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
       if (BF16) {
         reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(s);
