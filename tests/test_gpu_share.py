@@ -24,6 +24,10 @@ def _specs():
                                      top=(64, 32, 1), l_min=1, l_max=30),
         "sh_bf16": workload.FunctionSpec(key="sh_bf16", dtype="bf16", rows=[30000, 20000, 50000], dim=64,
                                          bot_dims=[128, 64], top_dims=[128, 64, 1], alpha=1.1, l_min=0, l_max=40),
+        # every hidden layer tiles by 64: the fp32 tensor-core path, whose split weight planes
+        # the attaching process computes itself once the owner reports the data complete
+        "sh_f32p": workload.spec_tiny(key="sh_f32p", dtype="f32", n_tables=4, rows=20000, dim=64, bot=(128, 64),
+                                      top=(128, 64, 1), l_min=1, l_max=30),
     }
 
 
@@ -130,7 +134,7 @@ def _local_outputs(spec):
     return outs
 
 
-@pytest.mark.parametrize("key", ["sh_f32", "sh_bf16"])
+@pytest.mark.parametrize("key", ["sh_f32", "sh_bf16", "sh_f32p"])
 def test_two_processes_map_one_staged_copy(key):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
