@@ -32,6 +32,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
                   "sm_max_mhz": 2032.0}
 SMS = 148
 FP32_LANES_PER_SM = 128
+TUNING_KINDS = {"1": "bf16", "2": "f32x3tf32", "3": "f32x3tf32_presplit", "4": "bottom01_f32"}
 
 
 # ------------------------------------------------------------------ workloads
@@ -450,7 +451,7 @@ def run_ours(args, rank, world, local_rank):
         "speedup_fused_vs_plain": round(value / (plain_rate * world), 3),
         "direct_launches": graphs_res,
         "setup": setup,
-        "tuning": [{"kind": "bf16" if t[0] == "1" else "f32x3tf32", "m_bucket": int(t[1]), "N": int(t[2]),
+        "tuning": [{"kind": TUNING_KINDS.get(t[0], t[0]), "m_bucket": int(t[1]), "N": int(t[2]),
                     "K": int(t[3]), "bn": int(t[4]), "stages": int(t[5])} for t in tuning],
         "kernels": kernels,
         "roofline": roof,

@@ -305,13 +305,19 @@ int sage_profile_read(sage_kernel_time* out, int max);
  * tensor-core layer of `fn` for a batch of `rows` samples (bucketed to the next
  * power of two) on scratch operands it allocates and frees, and records the
  * fastest per shape in a process-wide table that every later launch of that
- * shape uses.  Synchronous.  sage_tuning_save / _load write / read the table as
+ * shape uses; for an fp32 function whose bottom layers 0 and 1 can run as one
+ * kernel it also times that kernel against the two separate ones.  Synchronous.  sage_tuning_save / _load write / read the table as
  * text keyed by the GPU's name (entries for other GPUs are ignored on load). */
 sage_status sage_autotune(sage_fn fn, int rows, void* stream);
 /* Pin a tile configuration for GEMM shape (kind, batch rows bucket, N, K): kind 1 =
  * BF16, 2 = fp32 splitting in shared memory, 3 = fp32 from pre-split planes (the
  * fp32 functions' path; stages >= 100 selects the persistent kernel with stages-100
- * pipeline stages).  SAGE_ERR_INVALID for configurations the kernel does not have. */
+ * pipeline stages), 4 = bottom layers 0 and 1 of an fp32 function in one kernel
+ * (N = layer 1's outputs, K = layer 0's outputs; (bn, stages) = (256, 102),
+ * (128, 103) or (64, 104), or (1, 1) for separate kernels; fusable when layer 0
+ * has at most 16 inputs and at most 512 outputs, a multiple of 32, and every
+ * hidden layer runs on the tensor cores; untuned, fusable shapes run fused).
+ * SAGE_ERR_INVALID for configurations the kernel does not have. */
 sage_status sage_tuning_set(int kind, int rows, int N, int K, int bn, int stages);
 sage_status sage_tuning_save(const char* path);
 sage_status sage_tuning_load(const char* path);

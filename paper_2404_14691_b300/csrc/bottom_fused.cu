@@ -1,0 +1,328 @@
+// Bottom layers 0 and 1 of an fp32 function in one persistent kernel.
+//
+// Layer 0 (K0 <= 16 dense inputs -> N0 outputs, ReLU) has too little arithmetic for
+// the tensor cores and would otherwise write N0 activations per row (as two tf32
+// planes) only for layer 1 to read them back.  Here sixteen producer warps compute
+// each 128 x 32 k-block of layer 0's output straight into the shared-memory A
+// tiles of layer 1 -- tf32 hi / fp32 residual lo, in the 128-byte-swizzle layout
+// the TMA would have written -- while layer 1 runs on the tensor cores as three
+// tf32 products (hi.hi + hi.lo + lo.hi), exactly as the persistent kernel does:
+//   warp 0 lane 0 : TMA of layer 1's weight planes (B)
+//   warp 1 lane 0 : MMA issuer, two TMEM accumulators alternating between tiles
+//   warps 2-5     : epilogue (bias, ReLU, hi/lo planes of layer 1's output)
+//   warps 6-21    : producers, thread = row of the tile, four warps per row set
+//                   (each computing a quarter of a k-block's 32 columns)
+// Layer 0's arithmetic is bottom0's (fmaf chain over k = 0..15 with zero padding,
+// then + bias, ReLU), so the fused and separate forms give the same bits.
+#include "kernels.h"
+
+namespace sage {
+namespace {
+
+constexpr int kBM = 128, kBK = 32, kKM = 16, kW0Max = 512;
+// producer warps: kGroups sets of 4, set g computing chunks [g * 8 / kGroups, ...) of
+// each k-block's 8 16-byte column chunks for its 128 rows
+constexpr int kGroups = 4, kProducers = 128 * kGroups, kThreads = 192 + kProducers;
+
+template <int BN, int NST>
+struct B01Cfg {
+  static constexpr int A_BYTES = kBM * kBK * 4;
+  static constexpr int B_BYTES = BN * kBK * 4;
+  static constexpr int STAGE = 2 * (A_BYTES + B_BYTES);
+  static constexpr int W0_BYTES = kW0Max * kKM * 4;  // layer 0's weights, rows padded to 16
+  static constexpr int SMEM = NST * STAGE + W0_BYTES + 1024 + 512;
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+template <int BN, int NST>
+__global__ void __launch_bounds__(kThreads, 1)
+    bottom01_kernel(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                    const __grid_constant__ InvTable tab, int K0, int N0, const float* __restrict__ W0,
+                    const float* __restrict__ b0, int N1, const float* __restrict__ b1, float* __restrict__ Yh,
+                    float* __restrict__ Yl, int ldy, int* err) {
+  using C = B01Cfg<BN, NST>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = smem_align1024(smem_raw);
+  auto a_hi = [&](int s) { return smem + s * C::STAGE; };
+  auto b_hi = [&](int s) { return smem + s * C::STAGE + C::A_BYTES; };
+  auto a_lo = [&](int s) { return smem + s * C::STAGE + C::A_BYTES + C::B_BYTES; };
+  auto b_lo = [&](int s) { return smem + s * C::STAGE + 2 * C::A_BYTES + C::B_BYTES; };
+  float* sW0 = reinterpret_cast<float*>(smem + NST * C::STAGE);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * C::STAGE + C::W0_BYTES);
+  uint64_t* empty = full + NST;
+  uint64_t* acc_full = empty + NST;  // [2]
+  uint64_t* acc_empty = acc_full + 2;  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int M = tab.M;
+  const int KB = N0 / kBK;  // layer 1's reduction runs over layer 0's outputs
+  const int NT = N1 / BN, MT = (M + kBM - 1) / kBM;
+  const int tiles = NT * MT;
+
+  // layer 0's weights: coalesced reads of the contiguous [N0, K0] array into rows
+  // padded to 16 with zeros
+#pragma unroll 4
+  for (int e = threadIdx.x; e < N0 * K0; e += blockDim.x) sW0[(e / K0) * kKM + e % K0] = __ldg(W0 + e);
+  for (int e = threadIdx.x; e < N0 * (kKM - K0); e += blockDim.x)
+    sW0[(e / (kKM - K0)) * kKM + K0 + e % (kKM - K0)] = 0.f;
+  if (warp == 0) tmem_alloc(tmem_slot, 2 * BN);
+  if (warp == 1 && lane == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(&full[s], 1 + kProducers);  // the TMA thread + every producer thread
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 2 && lane == 0) {
+    tma_prefetch_desc(&tmBh);
+    tma_prefetch_desc(&tmBl);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int n0 = (t % NT) * BN;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % NST;
+          const uint32_t ph = (g / NST) & 1;
+          if (!mbar_wait(&empty[s], ph ^ 1, err)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&full[s], 2 * C::B_BYTES);
+          tma_load_2d(b_hi(s), &tmBh, kb * kBK, n0, &full[s]);
+          tma_load_2d(b_lo(s), &tmBl, kb * kBK, n0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32_f32(kBM, BN);
+      uint32_t g = 0;
+      int i = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+        const int buf = i & 1;
+        const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
+        if (!mbar_wait(&acc_empty[buf], ((i >> 1) & 1) ^ 1, err)) break;
+        tc_fence_after();
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % NST;
+          const uint32_t ph = (g / NST) & 1;
+          if (!mbar_wait(&full[s], ph, err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(a_hi(s)), bh = smem_u32(b_hi(s));
+          const uint32_t al = smem_u32(a_lo(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+          for (int k = 0; k < kBK / 8; ++k) {
+            const uint32_t o = k * 32;
+            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
+            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+            tc_mma_tf32(acc, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
+          }
+          tc_commit(&empty[s]);
+        }
+        tc_commit(&acc_full[buf]);
+      }
+    }
+  } else if (warp < 6) {
+    // ---- epilogue warps: layer 1's bias, ReLU, hi/lo planes
+    const int q = warp & 3;
+    int i = 0;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int buf = i & 1;
+      const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
+      tc_fence_after();
+      const int row = m0 + q * 32 + lane;
+      const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        tmem_ld_wait();
+        if (row < M) {
+          float4* dh = reinterpret_cast<float4*>(Yh + ro + c0);
+          float4* dl = reinterpret_cast<float4*>(Yl + ro + c0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) o[u] = fmaxf(__uint_as_float(v[4 * j + u]) + __ldg(b1 + n0 + c0 + 4 * j + u), 0.f);
+            float4 h, l;
+            h.x = to_tf32_rna(o[0]);
+            h.y = to_tf32_rna(o[1]);
+            h.z = to_tf32_rna(o[2]);
+            h.w = to_tf32_rna(o[3]);
+            l.x = o[0] - h.x;
+            l.y = o[1] - h.y;
+            l.z = o[2] - h.z;
+            l.w = o[3] - h.w;
+            dh[j] = h;
+            dl[j] = l;
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
+    }
+  } else {
+    // ---- producers: layer 0 for row pr of the tile, 32 columns per k-block, written
+    // as the A tiles' hi/lo planes (row pr: 8 chunks of 16 B, chunk c at slot c ^ (pr % 8))
+    const int pr = ((warp - 6) & 3) * 32 + lane;
+    const int c0 = ((warp - 6) >> 2) * (8 / kGroups);
+    const uint32_t rbase = static_cast<uint32_t>((pr >> 3) * 1024 + (pr & 7) * 128);
+    uint32_t g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int row = (t / NT) * kBM + pr;
+      float x[kKM];
+#pragma unroll
+      for (int k = 0; k < kKM; ++k) x[k] = 0.f;
+      if (row < M) {
+        const int inv = tab.n == 1 ? 0 : find_inv(tab, row);
+        const float* dense = tab.d[inv].dense + static_cast<size_t>(row - tab.d[inv].row_base) * K0;
+#pragma unroll
+        for (int k = 0; k < kKM; ++k)
+          if (k < K0) x[k] = __ldg(dense + k);
+      }
+      for (int kb = 0; kb < KB; ++kb, ++g) {
+        const int s = g % NST;
+        const uint32_t ph = (g / NST) & 1;
+        if (!mbar_wait(&empty[s], ph ^ 1, err)) {
+          ok = false;
+          break;
+        }
+        uint8_t* ah = a_hi(s);
+        uint8_t* al = a_lo(s);
+#pragma unroll 2
+        for (int c = c0; c < c0 + 8 / kGroups; ++c) {
+          float h[4], l[4];
+          const float4 bv = __ldg(reinterpret_cast<const float4*>(b0) + kb * (kBK / 4) + c);
+          const float bias[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = kb * kBK + c * 4 + u;
+            const float4* wv = reinterpret_cast<const float4*>(sW0 + j * kKM);
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < kKM / 4; ++q) {
+              const float4 w = wv[q];  // broadcast: every producer thread reads the same column
+              acc = fmaf(x[4 * q], w.x, acc);
+              acc = fmaf(x[4 * q + 1], w.y, acc);
+              acc = fmaf(x[4 * q + 2], w.z, acc);
+              acc = fmaf(x[4 * q + 3], w.w, acc);
+            }
+            const float y0 = fmaxf(acc + bias[u], 0.f);
+            h[u] = to_tf32_rna(y0);
+            l[u] = y0 - h[u];
+          }
+          const uint32_t off = rbase + ((static_cast<uint32_t>(c) ^ static_cast<uint32_t>(pr & 7)) << 4);
+          *reinterpret_cast<float4*>(ah + off) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(al + off) = make_float4(l[0], l[1], l[2], l[3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes -> the tensor cores' reads
+        mbar_arrive(&full[s]);
+      }
+    }
+  }
+  __syncwarp();
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 2 * BN);
+}
+
+int g_sms_b01 = 0;
+
+template <int BN, int NST>
+cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
+                       const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy, int* err,
+                       cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(bottom01_kernel<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         B01Cfg<BN, NST>::SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  if (!g_sms_b01) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_b01, cudaDevAttrMultiProcessorCount, dev);
+  }
+  CUtensorMap tbh, tbl;
+  if (!make_tmap_2d(&tbh, 0, w1h, N1, N0, N0, kBK, BN) || !make_tmap_2d(&tbl, 0, w1l, N1, N0, N0, kBK, BN))
+    return cudaErrorInvalidValue;
+  const int tiles = (N1 / BN) * ((tab.M + kBM - 1) / kBM);
+  const int grid = tiles < g_sms_b01 ? tiles : g_sms_b01;
+  bottom01_kernel<BN, NST><<<grid, kThreads, B01Cfg<BN, NST>::SMEM, s>>>(tbh, tbl, tab, K0, N0, W0, b0, N1, b1, yh, yl,
+                                                                     ldy, err);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool bottom01_fusable(int K0, int N0, int N1) {
+  return K0 >= 1 && K0 <= kKM && N0 >= kBK && N0 <= kW0Max && N0 % kBK == 0 && N1 % 64 == 0;
+}
+
+// Tile configurations: (BN, stages + 100), all persistent; BN = N1 computes layer 0
+// once per row, narrower tiles recompute it for each of the N1 / BN column tiles.
+const GemmCfg kB01Cfgs[] = {{256, 102}, {128, 103}, {64, 104}};
+
+int bottom01_candidates(GemmCfg* out, int max) {
+  int n = 0;
+  for (const GemmCfg& c : kB01Cfgs)
+    if (n < max) out[n++] = c;
+  if (n < max) out[n++] = GemmCfg{1, 1};  // separate kernels
+  return n;
+}
+
+GemmCfg bottom01_default(int N1) {
+  if (N1 % 256 == 0 && N1 <= 256) return GemmCfg{256, 102};
+  if (N1 % 128 == 0) return GemmCfg{128, 103};
+  return GemmCfg{64, 104};
+}
+
+cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
+                                const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy,
+                                int* err, cudaStream_t s, GemmCfg cfg) {
+  if (tab.M <= 0) return cudaSuccess;
+  if (!bottom01_fusable(K0, N0, N1) || (ldy % 4)) return cudaErrorInvalidValue;
+  for (const void* p : {static_cast<const void*>(w1h), static_cast<const void*>(w1l), static_cast<const void*>(yh),
+                        static_cast<const void*>(yl), static_cast<const void*>(b0)})
+    if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
+  if (cfg.bn == 0) cfg = bottom01_default(N1);
+  if (N1 % cfg.bn) return cudaErrorInvalidValue;
+  if (cfg.bn == 256 && cfg.stages == 102)
+    return launch_b01<256, 2>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s);
+  if (cfg.bn == 128 && cfg.stages == 103)
+    return launch_b01<128, 3>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s);
+  if (cfg.bn == 64 && cfg.stages == 104)
+    return launch_b01<64, 4>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s);
+  return cudaErrorInvalidValue;
+}
+
+void preload_bottom01_kernels() {
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, bottom01_kernel<256, 2>);
+  cudaFuncGetAttributes(&fa, bottom01_kernel<128, 3>);
+  cudaFuncGetAttributes(&fa, bottom01_kernel<64, 4>);
+}
+
+}  // namespace sage

@@ -472,6 +472,8 @@ int gemm_candidates(int kind, GemmCfg* out, int max) {
       if (n < max) out[n++] = c;
   } else if (kind == kGemmTf32Pre) {
     n = tf32_presplit_candidates(out, max);
+  } else if (kind == kBottom01) {
+    n = bottom01_candidates(out, max);
   } else {
     n = tf32_candidates(out, max);
   }

@@ -60,7 +60,7 @@ struct GemmCfg {
   int bn;
   int stages;
 };
-enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2, kGemmTf32Pre = 3 };
+enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2, kGemmTf32Pre = 3, kBottom01 = 4 };
 int gemm_candidates(int kind, GemmCfg* out, int max);
 int tf32_candidates(GemmCfg* out, int max);
 int tf32_presplit_candidates(GemmCfg* out, int max);
@@ -68,6 +68,8 @@ int tf32_presplit_candidates(GemmCfg* out, int max);
 GemmCfg tuned_gemm(int kind, int M, int N, int K);
 // Times every configuration of one shape and records the fastest.
 sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg* chosen, double* best_ms);
+// Fused bottom layers 0 and 1 against the separate kernels (kBottom01).
+sage_status autotune_bottom01(int M, int K0, int N0, int N1, cudaStream_t s, GemmCfg* chosen);
 
 // Dense layers y = act(x W^T + b).
 cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
@@ -93,6 +95,17 @@ cudaError_t launch_linear_f32_tc_presplit_head(int M, int N, int K, const float*
 cudaError_t launch_linear_bf16_tc_head(int M, int N, int K, const void* x, int ldx, const void* W,
                                        const float* bias, int relu, int* err, cudaStream_t s, GemmCfg cfg,
                                        const HeadParams& hp);
+// Bottom layers 0 and 1 of a pre-split fp32 function in one kernel: layer 0
+// (K0 <= 16 dense inputs, N0 outputs, ReLU) is computed into layer 1's shared-memory
+// A tiles; layer 1's output (N1 columns, ReLU) is written as hi/lo planes.  Same bits
+// as launch_bottom0 followed by launch_linear_f32_tc_presplit.  cfg: one of
+// bottom01_candidates' fused configurations, or {0, 0} for bottom01_default.
+bool bottom01_fusable(int K0, int N0, int N1);
+int bottom01_candidates(GemmCfg* out, int max);  // the last one, {1, 1}, means separate kernels
+GemmCfg bottom01_default(int N1);
+cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
+                                const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy,
+                                int* err, cudaStream_t s, GemmCfg cfg);
 // hi[i] = tf32(src[i]) (round to nearest), lo[i] = src[i] - hi[i].
 cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s);
 // fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.
@@ -105,6 +118,7 @@ void preload_gather_kernels();
 void preload_simt_kernels();
 void preload_tc_kernels();
 void preload_tf32_kernels();
+void preload_bottom01_kernels();
 
 // ---------------------------------------------------------------- cross-process sharing
 //

@@ -492,8 +492,18 @@ void stager_loop(sage_pool_s* P) {
 
 // ---------------------------------------------------------------- kernel timing
 
-enum ProfKind { kProfBottom0 = 0, kProfGemmF32, kProfGemmTc, kProfGather, kProfHead, kProfGemmTf32, kProfKinds };
-const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32", "gemm_tc", "gather", "head", "gemm_tf32x3"};
+enum ProfKind {
+  kProfBottom0 = 0,
+  kProfGemmF32,
+  kProfGemmTc,
+  kProfGather,
+  kProfHead,
+  kProfGemmTf32,
+  kProfBottom01,
+  kProfKinds
+};
+const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32",    "gemm_tc", "gather",
+                                            "head",    "gemm_tf32x3", "bottom01"};
 
 struct ProfRec {
   int kind;
@@ -545,6 +555,7 @@ double load_kernels_once() {
     preload_simt_kernels();
     preload_tc_kernels();
     preload_tf32_kernels();
+    preload_bottom01_kernels();
     g_load_ms = ms_since(t0);
     spent = g_load_ms;
   });
@@ -839,15 +850,31 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   SAGE_CK(cudaStreamWaitEvent(s.branch, s.fork, 0));
   const cudaStream_t main_stream = stream;
   if (overlap) stream = s.branch;
-  // bottom MLP (layer 0 reads each invocation's dense rows)
-  {
+  // bottom MLP (layer 0 reads each invocation's dense rows); on the pre-split fp32
+  // path layers 0 and 1 run as one kernel unless the tuning table says otherwise
+  int l1 = 1;
+  if (ps2 && nb >= 2 && bottom01_fusable(e->layers[0].in, e->layers[0].out, e->layers[1].out)) {
+    const Layer& L0 = e->layers[0];
+    const Layer& L1 = e->layers[1];
+    const GemmCfg c = tuned_gemm(kBottom01, M, L1.out, L1.in);
+    if (c.bn != 1) {
+      void* y = nb == 2 ? bot_out : s.bot[1];
+      const int ldy = nb == 2 ? cd : e->bot[1];
+      ProfScope ps(stream, kProfBottom01, 2.0 * M * (L0.in * L0.out + L1.in * L1.out));
+      SAGE_CK(launch_bottom01_f32(tab, L0.in, L0.out, static_cast<const float*>(L0.W), L0.b, L1.out,
+                                  e->wplanes[1].first, e->wplanes[1].second, L1.b, static_cast<float*>(y),
+                                  lo_of(y, ldy), ldy, e->d_err, stream, c));
+      l1 = 2;
+    }
+  }
+  if (l1 == 1) {
     const Layer& L0 = e->layers[0];
     void* y = nb == 1 ? bot_out : s.bot[0];
     const int ldy = nb == 1 ? cd : e->bot[0];
     ProfScope ps(stream, kProfBottom0, 2.0 * M * L0.in * L0.out);
     SAGE_CK(launch_bottom0(e->dtype, tab, L0.in, L0.out, L0.W, L0.b, y, ldy, stream, lo_of(y, ldy)));
   }
-  for (int l = 1; l < nb; ++l) {
+  for (int l = l1; l < nb; ++l) {
     const Layer& L = e->layers[l];
     const void* x = s.bot[l - 1];
     void* y = l == nb - 1 ? bot_out : s.bot[l];
@@ -1687,6 +1714,8 @@ sage_status sage_autotune(sage_fn f, int rows, void* stream) {
     sage_status st = autotune_gemm(kind, rows, L.out, L.in, s, nullptr, nullptr);
     if (st != SAGE_OK) return st;
   }
+  if (e->presplit && nb >= 2 && bottom01_fusable(e->layers[0].in, e->layers[0].out, e->layers[1].out))
+    return autotune_bottom01(rows, e->layers[0].in, e->layers[0].out, e->layers[1].out, s, nullptr);
   return SAGE_OK;
 }
 

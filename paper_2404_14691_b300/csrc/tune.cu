@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -130,6 +131,88 @@ sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg
   }
   if (chosen) *chosen = best;
   if (best_ms) *best_ms = best_t;
+  return SAGE_OK;
+}
+
+// Bottom layers 0 and 1 of a pre-split fp32 function (K0 dense inputs, N0 and N1
+// outputs): times the fused kernel's tiles against bottom0 followed by layer 1's
+// GEMM at its own tuned tile (so tune that GEMM first) and records the fastest
+// under (kBottom01, M bucket, N1, N0); {1, 1} records that separate kernels won.
+sage_status autotune_bottom01(int M, int K0, int N0, int N1, cudaStream_t s, GemmCfg* chosen) {
+  if (!bottom01_fusable(K0, N0, N1)) return set_last_error("autotune: shape cannot fuse"), SAGE_ERR_INVALID;
+  const int Mb = bucket(M);
+  const size_t sizes[] = {static_cast<size_t>(Mb) * K0, static_cast<size_t>(N0) * K0, static_cast<size_t>(N0),
+                          static_cast<size_t>(N1) * N0, static_cast<size_t>(N1), 2 * static_cast<size_t>(Mb) * N0,
+                          2 * static_cast<size_t>(Mb) * N1, 64};
+  constexpr int kBufs = sizeof(sizes) / sizeof(sizes[0]);
+  float* b[kBufs] = {};
+  auto cleanup = [&] {
+    for (float* p : b) cudaFree(p);
+  };
+  for (int i = 0; i < kBufs; ++i) {
+    if (cudaMalloc(&b[i], sizes[i] * 4) != cudaSuccess) {
+      cleanup();
+      cudaGetLastError();
+      return set_last_error("autotune: scratch allocation failed"), SAGE_ERR_NOMEM;
+    }
+    cudaMemsetAsync(b[i], i == kBufs - 1 ? 0 : 0x3c, sizes[i] * 4, s);
+  }
+  float *dense = b[0], *w0 = b[1], *b0 = b[2], *w1 = b[3], *b1 = b[4], *y0 = b[5], *y1 = b[6];
+  int* err = reinterpret_cast<int*>(b[7]);
+  std::unique_ptr<InvTable> tab(new InvTable());
+  tab->n = 1;
+  tab->M = Mb;
+  tab->d[0] = InvDesc{dense, nullptr, nullptr, nullptr, Mb, 0, 0};
+  const GemmCfg g1 = tuned_gemm(kGemmTf32Pre, Mb, N1, N0);
+  GemmCfg cands[16];
+  const int nc = bottom01_candidates(cands, 16);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  GemmCfg best{0, 0};
+  float best_t = 1e30f;
+  for (int c = 0; c < nc; ++c) {
+    if (N1 % cands[c].bn) continue;
+    auto run = [&]() -> cudaError_t {
+      if (cands[c].bn == 1) {
+        cudaError_t ce = launch_bottom0(0, *tab, K0, N0, w0, b0, y0, N0, s, y0 + static_cast<size_t>(Mb) * N0);
+        if (ce != cudaSuccess) return ce;
+        return launch_linear_f32_tc_presplit(Mb, N1, N0, y0, y0 + static_cast<size_t>(Mb) * N0, N0, w1, w1, b1, 1,
+                                             y1, y1 + static_cast<size_t>(Mb) * N1, N1, err, s, g1);
+      }
+      return launch_bottom01_f32(*tab, K0, N0, w0, b0, N1, w1, w1, b1, y1, y1 + static_cast<size_t>(Mb) * N1, N1,
+                                 err, s, cands[c]);
+    };
+    if (run() != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    std::vector<float> t;
+    for (int r = 0; r < 5; ++r) {
+      cudaEventRecord(e0, s);
+      run();
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    if (t[2] < best_t) {
+      best_t = t[2];
+      best = cands[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaError_t ce = cudaStreamSynchronize(s);
+  cleanup();
+  if (ce != cudaSuccess) return set_last_error("autotune: a timing run failed"), SAGE_ERR_CUDA;
+  if (best.bn) {
+    std::lock_guard<std::mutex> g(g_mu);
+    g_table[Key{kBottom01, Mb, N1, N0}] = best;
+  }
+  if (chosen) *chosen = best;
   return SAGE_OK;
 }
 

@@ -1,0 +1,159 @@
+"""Bottom layers 0 and 1 of a pre-split fp32 function fused into one kernel: layer 0
+(Sec. 6 workload: 13 dense features into the bottom MLP) is computed straight into
+the A tiles of layer 1's tensor-core GEMM.  Every fused tile configuration gives the
+bits of the two separate kernels (bottom0, then the pre-split GEMM), and the
+function still matches the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+from helpers import RTOL, DevInvocation, prepare, to_f64
+
+pytestmark = pytest.mark.gpu
+
+sage = pytest.importorskip("paper_2404_14691_b300")
+
+KIND_BOTTOM01 = 4
+SEPARATE = (1, 1)
+FUSED = [(256, 102), (128, 103), (64, 104)]
+
+
+@pytest.fixture(scope="module")
+def pool():
+    p = sage.Pool(device=0)
+    yield p
+    p.destroy()
+
+
+def _spec(key, n_dense, bot, top=(128, 64, 1), dim=32):
+    s = workload.spec_tiny(key=key, dtype="f32", n_tables=3, rows=4000, dim=dim, bot=bot, top=top,
+                           l_min=0, l_max=30)
+    s.n_dense = n_dense
+    return s
+
+
+# (n_dense, bottom dims): the batching workload's bottom MLP; two-layer bottoms whose
+# layer 1 writes the concat buffer directly; the narrowest and widest layer 0
+CASES = [
+    ("b01_c2", 13, (512, 256, 64)),
+    ("b01_two", 16, (64, 128)),
+    ("b01_k1", 1, (32, 64, 64)),
+    ("b01_n0max", 7, (512, 64)),
+]
+
+
+def _same(a, b):
+    import torch
+    return torch.equal(a.out[:a.batch], b.out[:b.batch])
+
+
+def _run(f, invs):
+    import torch
+    d = [DevInvocation(v) for v in invs]
+    f.invoke_batch([x.args() for x in d])
+    torch.cuda.synchronize()
+    f.check_errors()
+    return d
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_fused_bottom_equals_separate_kernels_bitwise(pool, case):
+    key, n_dense, bot = case
+    spec = _spec(key, n_dense, bot)
+    f = prepare(pool, spec, max_batch=4096)
+    try:
+        # ragged members (an empty one, a single row) so the last M tile is partial
+        sizes = [700, 0, 1, 333, 129]
+        invs = [workload.make_invocation(spec, B, seed=900 + i) for i, B in enumerate(sizes)]
+        M = sum(sizes)
+        N0, N1 = bot[0], bot[1]
+        sage.tuning_set(KIND_BOTTOM01, M, N1, N0, *SEPARATE)
+        ref = _run(f, invs)
+        for tile in FUSED:
+            if N1 % tile[0]:
+                continue
+            sage.tuning_set(KIND_BOTTOM01, M, N1, N0, *tile)
+            got = _run(f, invs)
+            for a, b in zip(ref, got):
+                assert _same(a, b), (tile, a.batch)
+        # one invocation alone (the kernel skips the invocation search) equals its batch row range
+        one = _run(f, [invs[3]])
+        assert _same(one[0], ref[3])
+        tables = [workload.full_table(spec, t) for t in range(spec.n_tables)]
+        w = workload.weights_arrays(spec)
+        for d in (got[0], got[2], got[4]):
+            res = oracle.forward(spec, w, d.inv, tables=tables, want_pooled=False)
+            c = oracle.check_close(to_f64(d.out)[:d.batch], res["out"], res["out_mag"], RTOL["f32"])
+            assert c["ok"], c
+    finally:
+        f.release()
+
+
+def test_fused_bottom_is_the_default_and_counts_one_launch(pool):
+    """Untuned, a fusable pre-split function runs layers 0 and 1 as one kernel: one launch
+    fewer per batch than with separate kernels pinned."""
+    spec = _spec("b01_launches", 13, (512, 256, 64))
+    f = prepare(pool, spec, max_batch=4096)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=950 + i) for i, B in enumerate([300, 211])]
+        M = 511
+        _run(f, invs)
+        n0 = sage.kernel_launches()
+        a = _run(f, invs)
+        fused = sage.kernel_launches() - n0
+        sage.tuning_set(KIND_BOTTOM01, M, 256, 512, *SEPARATE)
+        n0 = sage.kernel_launches()
+        b = _run(f, invs)
+        separate = sage.kernel_launches() - n0
+        assert separate == fused + 1
+        for x, y in zip(a, b):
+            assert _same(x, y)
+    finally:
+        f.release()
+
+
+def test_autotune_chooses_a_bottom_form_and_keeps_bits(pool, tmp_path):
+    spec = _spec("b01_tune", 13, (512, 256, 64))
+    f = prepare(pool, spec, max_batch=4096)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=970 + i) for i, B in enumerate([1500, 900])]
+        before = _run(f, invs)
+        f.autotune(2400)
+        after = _run(f, invs)
+        for x, y in zip(before, after):
+            assert _same(x, y)
+        path = str(tmp_path / "tune.txt")
+        sage.tuning_save(path)
+        rows = [l.split() for l in open(path) if not l.startswith("#")]
+        b01 = [r for r in rows if r[1:5] == [str(KIND_BOTTOM01), "4096", "256", "512"]]
+        assert len(b01) == 1
+        assert (int(b01[0][5]), int(b01[0][6])) in FUSED + [SEPARATE]
+    finally:
+        f.release()
+
+
+def test_unknown_bottom_tile_is_refused():
+    with pytest.raises(sage.SageError):
+        sage.tuning_set(KIND_BOTTOM01, 512, 256, 512, 128, 3)
+    with pytest.raises(sage.SageError):
+        sage.tuning_set(KIND_BOTTOM01, 512, 192, 512, 128, 103)   # 192 is not a multiple of 128
+
+
+def test_fused_bottom_dense_rows_beyond_alignment(pool):
+    """Dense rows of 13 floats start at every 4-byte offset; the fused kernel reads them
+    element by element, so odd row starts are fine."""
+    spec = _spec("b01_align", 13, (64, 64))
+    f = prepare(pool, spec, max_batch=4096)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=990 + i) for i, B in enumerate([3, 5, 7, 11])]
+        M = 26
+        sage.tuning_set(KIND_BOTTOM01, M, 64, 64, *SEPARATE)
+        ref = _run(f, invs)
+        sage.tuning_set(KIND_BOTTOM01, M, 64, 64, 64, 104)
+        got = _run(f, invs)
+        for a, b in zip(ref, got):
+            assert _same(a, b)
+        assert np.isfinite(to_f64(got[0].out)[:3]).all()
+    finally:
+        f.release()
