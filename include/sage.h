@@ -315,7 +315,7 @@ sage_status sage_autotune(sage_fn fn, int rows, void* stream);
  * pipeline stages), 4 = bottom layers 0 and 1 of an fp32 function in one kernel
  * (N = layer 1's outputs, K = layer 0's outputs; (bn, stages) = (256, 102),
  * (128, 103) or (64, 104), or (1, 1) for separate kernels; fusable when layer 0
- * has at most 16 inputs and at most 512 outputs, a multiple of 32, and every
+ * has at most 15 inputs and at most 512 outputs, a multiple of 32, and every
  * hidden layer runs on the tensor cores; untuned, fusable shapes run fused).
  * SAGE_ERR_INVALID for configurations the kernel does not have. */
 sage_status sage_tuning_set(int kind, int rows, int N, int K, int bn, int stages);

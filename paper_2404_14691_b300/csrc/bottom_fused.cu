@@ -1,6 +1,6 @@
 // Bottom layers 0 and 1 of an fp32 function in one persistent kernel.
 //
-// Layer 0 (K0 <= 16 dense inputs -> N0 outputs, ReLU) has too little arithmetic for
+// Layer 0 (K0 <= 15 dense inputs -> N0 outputs, ReLU) has too little arithmetic for
 // the tensor cores and would otherwise write N0 activations per row (as two tf32
 // planes) only for layer 1 to read them back.  Here sixteen producer warps compute
 // each 128 x 32 k-block of layer 0's output straight into the shared-memory A
@@ -9,11 +9,16 @@
 // tf32 products (hi.hi + hi.lo + lo.hi), exactly as the persistent kernel does:
 //   warp 0 lane 0 : TMA of layer 1's weight planes (B)
 //   warp 1 lane 0 : MMA issuer, two TMEM accumulators alternating between tiles
-//   warps 2-5     : epilogue (bias, ReLU, hi/lo planes of layer 1's output)
+//   warps 2-5     : epilogue (bias, ReLU, hi/lo planes of layer 1's output; a CTA's
+//                   last tile leaves through the idle stage ring and TMA stores)
 //   warps 6-21    : producers, thread = row of the tile, four warps per row set
 //                   (each computing a quarter of a k-block's 32 columns)
 // Layer 0's arithmetic is bottom0's (fmaf chain over k = 0..15 with zero padding,
-// then + bias, ReLU), so the fused and separate forms give the same bits.
+// then + bias, ReLU), so the fused and separate forms give the same bits.  The bias
+// sits in weight slot K0 against an input of 1: fmaf(1, b, s) rounds s + b once, as
+// the separate kernel's addition does, and the zero-padded terms after it leave the
+// sum unchanged (an fmaf chain from +0 reaches -0 only by underflow), so no global
+// load remains in the producers' loop.
 #include "kernels.h"
 
 namespace sage {
@@ -32,11 +37,13 @@ struct B01Cfg {
   static constexpr int W0_BYTES = kW0Max * kKM * 4;  // layer 0's weights, rows padded to 16
   static constexpr int SMEM = NST * STAGE + W0_BYTES + 1024 + 512;
   static_assert(SMEM <= 232448, "shared memory");
+  static_assert(NST * STAGE >= 4 * 32768, "last-tile output staging: 32 KB per epilogue warp");
 };
 
 template <int BN, int NST>
 __global__ void __launch_bounds__(kThreads, 1)
     bottom01_kernel(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                    const __grid_constant__ CUtensorMap tmYh, const __grid_constant__ CUtensorMap tmYl,
                     const __grid_constant__ InvTable tab, int K0, int N0, const float* __restrict__ W0,
                     const float* __restrict__ b0, int N1, const float* __restrict__ b1, float* __restrict__ Yh,
                     float* __restrict__ Yl, int ldy, int* err) {
@@ -60,12 +67,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int NT = N1 / BN, MT = (M + kBM - 1) / kBM;
   const int tiles = NT * MT;
 
-  // layer 0's weights: coalesced reads of the contiguous [N0, K0] array into rows
-  // padded to 16 with zeros
-#pragma unroll 4
-  for (int e = threadIdx.x; e < N0 * K0; e += blockDim.x) sW0[(e / K0) * kKM + e % K0] = __ldg(W0 + e);
-  for (int e = threadIdx.x; e < N0 * (kKM - K0); e += blockDim.x)
-    sW0[(e / (kKM - K0)) * kKM + K0 + e % (kKM - K0)] = 0.f;
   if (warp == 0) tmem_alloc(tmem_slot, 2 * BN);
   if (warp == 1 && lane == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -81,6 +82,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 2 && lane == 0) {
     tma_prefetch_desc(&tmBh);
     tma_prefetch_desc(&tmBl);
+    tma_prefetch_desc(&tmYh);
+    tma_prefetch_desc(&tmYl);
   }
   tc_fence_before();
   __syncthreads();
@@ -149,11 +152,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
       tc_fence_after();
       const int row = m0 + q * 32 + lane;
+      const uint32_t tm = tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16);
+      if (t + static_cast<int>(gridDim.x) >= tiles) {
+        // the CTA's last tile: out through the idle stage ring and TMA stores
+        tail_store_f32_planes<BN>(tm, smem + q * 32768, lane, b1, true, &tmYh, &tmYl, n0, m0 + q * 32,
+                                  m0 + q * 32 < M);
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+        continue;
+      }
       const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t v[32];
-        tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
+        tmem_ld_32cols(tm + c0, v);
         tmem_ld_wait();
         if (row < M) {
           float4* dh = reinterpret_cast<float4*>(Yh + ro + c0);
@@ -183,6 +195,23 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- producers: layer 0 for row pr of the tile, 32 columns per k-block, written
     // as the A tiles' hi/lo planes (row pr: 8 chunks of 16 B, chunk c at slot c ^ (pr % 8))
+    {
+      // layer 0's weights into rows of 16 -- weights, the bias (slot K0), zeros -- with
+      // every load in flight before the first store; then wait for the producers only
+      const int pt = threadIdx.x - 192;
+      constexpr int kPer = kW0Max * kKM / kProducers;
+      static_assert(kW0Max * kKM % kProducers == 0, "weight staging split");
+      float w[kPer];
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int e = pt + i * kProducers, j = e / kKM, k = e % kKM;
+        w[i] = j >= N0 ? 0.f : k < K0 ? __ldg(W0 + j * K0 + k) : k == K0 ? __ldg(b0 + j) : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < kPer; ++i)
+        if (pt + i * kProducers < N0 * kKM) sW0[pt + i * kProducers] = w[i];
+      named_barrier_sync(1, kProducers);
+    }
     const int pr = ((warp - 6) & 3) * 32 + lane;
     const int c0 = ((warp - 6) >> 2) * (8 / kGroups);
     const uint32_t rbase = static_cast<uint32_t>((pr >> 3) * 1024 + (pr & 7) * 128);
@@ -192,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row = (t / NT) * kBM + pr;
       float x[kKM];
 #pragma unroll
-      for (int k = 0; k < kKM; ++k) x[k] = 0.f;
+      for (int k = 0; k < kKM; ++k) x[k] = k == K0 ? 1.f : 0.f;
       if (row < M) {
         const int inv = tab.n == 1 ? 0 : find_inv(tab, row);
         const float* dense = tab.d[inv].dense + static_cast<size_t>(row - tab.d[inv].row_base) * K0;
@@ -212,8 +241,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 2
         for (int c = c0; c < c0 + 8 / kGroups; ++c) {
           float h[4], l[4];
-          const float4 bv = __ldg(reinterpret_cast<const float4*>(b0) + kb * (kBK / 4) + c);
-          const float bias[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
             const int j = kb * kBK + c * 4 + u;
@@ -227,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               acc = fmaf(x[4 * q + 2], w.z, acc);
               acc = fmaf(x[4 * q + 3], w.w, acc);
             }
-            const float y0 = fmaxf(acc + bias[u], 0.f);
+            const float y0 = fmaxf(acc, 0.f);
             h[u] = to_tf32_rna(y0);
             l[u] = y0 - h[u];
           }
@@ -264,12 +291,13 @@ cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, con
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms_b01, cudaDevAttrMultiProcessorCount, dev);
   }
-  CUtensorMap tbh, tbl;
-  if (!make_tmap_2d(&tbh, 0, w1h, N1, N0, N0, kBK, BN) || !make_tmap_2d(&tbl, 0, w1l, N1, N0, N0, kBK, BN))
+  CUtensorMap tbh, tbl, tyh, tyl;
+  if (!make_tmap_2d(&tbh, 0, w1h, N1, N0, N0, kBK, BN) || !make_tmap_2d(&tbl, 0, w1l, N1, N0, N0, kBK, BN) ||
+      !make_tmap_2d(&tyh, 0, yh, tab.M, N1, ldy, 32, 32) || !make_tmap_2d(&tyl, 0, yl, tab.M, N1, ldy, 32, 32))
     return cudaErrorInvalidValue;
   const int tiles = (N1 / BN) * ((tab.M + kBM - 1) / kBM);
   const int grid = tiles < g_sms_b01 ? tiles : g_sms_b01;
-  bottom01_kernel<BN, NST><<<grid, kThreads, B01Cfg<BN, NST>::SMEM, s>>>(tbh, tbl, tab, K0, N0, W0, b0, N1, b1, yh, yl,
+  bottom01_kernel<BN, NST><<<grid, kThreads, B01Cfg<BN, NST>::SMEM, s>>>(tbh, tbl, tyh, tyl, tab, K0, N0, W0, b0, N1, b1, yh, yl,
                                                                      ldy, err);
   count_launch();
   return cudaGetLastError();
@@ -278,7 +306,7 @@ cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, con
 }  // namespace
 
 bool bottom01_fusable(int K0, int N0, int N1) {
-  return K0 >= 1 && K0 <= kKM && N0 >= kBK && N0 <= kW0Max && N0 % kBK == 0 && N1 % 64 == 0;
+  return K0 >= 1 && K0 < kKM && N0 >= kBK && N0 <= kW0Max && N0 % kBK == 0 && N1 % 64 == 0;
 }
 
 // Tile configurations: (BN, stages + 100), all persistent; BN = N1 computes layer 0
@@ -305,7 +333,7 @@ cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float
   if (tab.M <= 0) return cudaSuccess;
   if (!bottom01_fusable(K0, N0, N1) || (ldy % 4)) return cudaErrorInvalidValue;
   for (const void* p : {static_cast<const void*>(w1h), static_cast<const void*>(w1l), static_cast<const void*>(yh),
-                        static_cast<const void*>(yl), static_cast<const void*>(b0)})
+                        static_cast<const void*>(yl)})
     if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
   if (cfg.bn == 0) cfg = bottom01_default(N1);
   if (N1 % cfg.bn) return cudaErrorInvalidValue;

@@ -193,6 +193,28 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const void* tmap, in
       : "memory");
 }
 
+// 2-D tiled bulk tensor store shared -> global (rows outside the tensor map are
+// not written), tracked as a bulk group of the issuing thread.
+__device__ __forceinline__ void tma_store_2d(const void* tmap, const void* smem_src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(tmap)),
+               "r"(smem_u32(smem_src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most N of this thread's bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void tma_store_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+// Wait until all of this thread's bulk groups have completed their writes.
+__device__ __forceinline__ void tma_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Barrier over the `count` threads (a multiple of 32) that use barrier `id` (1..15).
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 __device__ __forceinline__ void tma_prefetch_desc(const void* tmap) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tmap)) : "memory");
 }
@@ -309,5 +331,68 @@ __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&r)[32]
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ---------------------------------------------------------------- tail epilogue
+//
+// Output of a persistent GEMM's last tile (per CTA) as tf32 hi / fp32 lo planes,
+// y = act(acc + bias).  When that tile's MMAs have completed the CTA's stage ring
+// is idle, so each epilogue warp stages its 32 rows x 32 columns there (128-byte
+// swizzle: row r's 16-byte chunk j at r * 128 + ((j ^ r % 8) * 16), conflict-free)
+// and writes them with TMA stores: whole 128-byte row pieces instead of a 16-byte
+// piece of 32 different rows per store instruction.  `stg` is the warp's 32 KB
+// (four hi/lo buffer pairs, 1024-byte aligned); `tm` its TMEM lanes at column 0;
+// (x0, y0) the block's first column and row in the output; `live` false when all
+// 32 rows lie beyond the output (nothing is stored).  Same arithmetic as the
+// direct stores, so the same bits.
+template <int BN>
+__device__ __forceinline__ void tail_store_f32_planes(uint32_t tm, uint8_t* stg, int lane,
+                                                      const float* __restrict__ bias, bool relu,
+                                                      const void* tmYh, const void* tmYl, int x0, int y0,
+                                                      bool live) {
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld_32cols(tm + c0, v);
+    tmem_ld_wait();
+    uint8_t* hb = stg + ((c0 / 32) & 3) * 8192;
+    uint8_t* lb = hb + 4096;
+    if (c0 >= 128) {
+      if (lane == 0) tma_store_wait_read<3>();  // this pair's stores of four blocks ago
+      __syncwarp();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        o[u] = __uint_as_float(v[4 * j + u]) + __ldg(bias + x0 + c0 + 4 * j + u);
+        if (relu) o[u] = fmaxf(o[u], 0.f);
+      }
+      float4 h, l;
+      h.x = to_tf32_rna(o[0]);
+      h.y = to_tf32_rna(o[1]);
+      h.z = to_tf32_rna(o[2]);
+      h.w = to_tf32_rna(o[3]);
+      l.x = o[0] - h.x;
+      l.y = o[1] - h.y;
+      l.z = o[2] - h.z;
+      l.w = o[3] - h.w;
+      const uint32_t off = static_cast<uint32_t>(lane * 128 + ((j ^ (lane & 7)) << 4));
+      *reinterpret_cast<float4*>(hb + off) = h;
+      *reinterpret_cast<float4*>(lb + off) = l;
+    }
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      if (live) {
+        tma_store_2d(tmYh, hb, x0 + c0, y0);
+        tma_store_2d(tmYl, lb, x0 + c0, y0);
+      }
+      tma_store_commit();
+    }
+  }
+  if (lane == 0) tma_store_wait_all();
+  __syncwarp();
+}
 
 }  // namespace sage

@@ -319,10 +319,12 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
                                                        const CUtensorMap& tmBh, const CUtensorMap& tmBl, int M,
                                                        int N, int K, const float* __restrict__ bias, int relu,
                                                        float* __restrict__ Yh, float* __restrict__ Yl, int ldy,
-                                                       int* err, const HeadParams* hp) {
+                                                       int* err, const HeadParams* hp, const CUtensorMap* tmYh,
+                                                       const CUtensorMap* tmYl) {
   using C = Tf32Cfg<BN, NST>;
+  static_assert(HEAD || C::STAGES * C::STAGE >= 4 * 32768, "last-tile output staging: 32 KB per epilogue warp");
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* smem = smem_align1024(smem_raw);
   auto a_hi = [&](int s) { return smem + s * C::STAGE; };
   auto b_hi = [&](int s) { return smem + s * C::STAGE + C::A_BYTES; };
   auto a_lo = [&](int s) { return smem + s * C::STAGE + C::A_BYTES + C::B_BYTES; };
@@ -457,6 +459,15 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
         if (row < M) head_row<BN / 64>(*hp, row, gs, static_cast<unsigned>(n0 / 64), G);
         continue;
       }
+      if (t + static_cast<int>(gridDim.x) >= tiles) {
+        // the CTA's last tile: out through the idle stage ring and TMA stores
+        tail_store_f32_planes<BN>(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16),
+                                  smem + q * 32768, lane, bias, relu != 0, tmYh, tmYl, n0, m0 + q * 32,
+                                  m0 + q * 32 < M);
+        tc_fence_before();
+        mbar_arrive(&acc_empty[buf]);
+        continue;
+      }
       const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
@@ -503,9 +514,11 @@ template <int BN, int NST>
 __global__ void __launch_bounds__(192, 1)
     gemm_tf32x3_persistent_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
+                                  const __grid_constant__ CUtensorMap tmYh, const __grid_constant__ CUtensorMap tmYl,
                                   int M, int N, int K, const float* __restrict__ bias, int relu,
                                   float* __restrict__ Yh, float* __restrict__ Yl, int ldy, int* err) {
-  tf32x3_persistent_body<BN, NST, false>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, Yh, Yl, ldy, err, nullptr);
+  tf32x3_persistent_body<BN, NST, false>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, Yh, Yl, ldy, err, nullptr,
+                                         &tmYh, &tmYl);
 }
 
 template <int BN, int NST>
@@ -516,7 +529,8 @@ __global__ void __launch_bounds__(192, 1)
                                        const __grid_constant__ CUtensorMap tmBl, int M, int N, int K,
                                        const float* __restrict__ bias, int relu, int* err,
                                        const __grid_constant__ HeadParams hp) {
-  tf32x3_persistent_body<BN, NST, true>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, nullptr, nullptr, 0, err, &hp);
+  tf32x3_persistent_body<BN, NST, true>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, nullptr, nullptr, 0, err, &hp,
+                                        nullptr, nullptr);
 }
 
 __global__ void split_planes_kernel(const float* __restrict__ src, float* __restrict__ hi, float* __restrict__ lo,
@@ -570,14 +584,15 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const float* xh, const flo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms_p, cudaDevAttrMultiProcessorCount, dev);
   }
-  CUtensorMap tah, tal, tbh, tbl;
+  CUtensorMap tah, tal, tbh, tbl, tyh, tyl;
   if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
-      !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN))
+      !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN) ||
+      !make_tmap_2d(&tyh, 0, yh, M, N, ldy, 32, 32) || !make_tmap_2d(&tyl, 0, yl, M, N, ldy, 32, 32))
     return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
   const int grid = tiles < g_sms_p ? tiles : g_sms_p;
-  gemm_tf32x3_persistent_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(tah, tal, tbh, tbl, M, N, K,
-                                                                                   bias, relu, yh, yl, ldy, err);
+  gemm_tf32x3_persistent_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(
+      tah, tal, tbh, tbl, tyh, tyl, M, N, K, bias, relu, yh, yl, ldy, err);
   count_launch();
   return cudaGetLastError();
 }

@@ -96,7 +96,7 @@ cudaError_t launch_linear_bf16_tc_head(int M, int N, int K, const void* x, int l
                                        const float* bias, int relu, int* err, cudaStream_t s, GemmCfg cfg,
                                        const HeadParams& hp);
 // Bottom layers 0 and 1 of a pre-split fp32 function in one kernel: layer 0
-// (K0 <= 16 dense inputs, N0 outputs, ReLU) is computed into layer 1's shared-memory
+// (K0 <= 15 dense inputs, N0 outputs, ReLU) is computed into layer 1's shared-memory
 // A tiles; layer 1's output (N1 columns, ReLU) is written as hi/lo planes.  Same bits
 // as launch_bottom0 followed by launch_linear_f32_tc_presplit.  cfg: one of
 // bottom01_candidates' fused configurations, or {0, 0} for bottom01_default.

@@ -37,7 +37,7 @@ def _spec(key, n_dense, bot, top=(128, 64, 1), dim=32):
 # layer 1 writes the concat buffer directly; the narrowest and widest layer 0
 CASES = [
     ("b01_c2", 13, (512, 256, 64)),
-    ("b01_two", 16, (64, 128)),
+    ("b01_two", 15, (64, 128)),
     ("b01_k1", 1, (32, 64, 64)),
     ("b01_n0max", 7, (512, 64)),
 ]
@@ -155,5 +155,29 @@ def test_fused_bottom_dense_rows_beyond_alignment(pool):
         for a, b in zip(ref, got):
             assert _same(a, b)
         assert np.isfinite(to_f64(got[0].out)[:3]).all()
+    finally:
+        f.release()
+
+
+def test_sixteen_dense_inputs_run_as_separate_kernels(pool):
+    """Layer 0 with 16 inputs leaves no weight slot for the bias: the function runs
+    bottom0 and the GEMM separately (same launch count as with separate kernels pinned)
+    and still matches the oracle."""
+    spec = _spec("b01_k16", 16, (64, 128))
+    f = prepare(pool, spec, max_batch=4096)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=1010 + i) for i, B in enumerate([200, 57])]
+        _run(f, invs)
+        n0 = sage.kernel_launches()
+        got = _run(f, invs)
+        default = sage.kernel_launches() - n0
+        sage.tuning_set(KIND_BOTTOM01, 257, 128, 64, *SEPARATE)
+        n0 = sage.kernel_launches()
+        _run(f, invs)
+        assert sage.kernel_launches() - n0 == default
+        tables = [workload.full_table(spec, t) for t in range(spec.n_tables)]
+        res = oracle.forward(spec, workload.weights_arrays(spec), got[1].inv, tables=tables, want_pooled=False)
+        c = oracle.check_close(to_f64(got[1].out)[:got[1].batch], res["out"], res["out_mag"], RTOL["f32"])
+        assert c["ok"], c
     finally:
         f.release()
