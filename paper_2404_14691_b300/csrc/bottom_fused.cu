@@ -37,7 +37,7 @@ struct B01Cfg {
   static constexpr int W0_BYTES = kW0Max * kKM * 4;  // layer 0's weights, rows padded to 16
   static constexpr int SMEM = NST * STAGE + W0_BYTES + 1024 + 512;
   static_assert(SMEM <= 232448, "shared memory");
-  static_assert(NST * STAGE >= 4 * 32768, "last-tile output staging: 32 KB per epilogue warp");
+  static_assert(NST * STAGE >= 20 * 8192, "last-tile output staging: 8 KB per epilogue and producer warp");
 };
 
 template <int BN, int NST>
@@ -154,9 +154,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row = m0 + q * 32 + lane;
       const uint32_t tm = tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16);
       if (t + static_cast<int>(gridDim.x) >= tiles) {
-        // the CTA's last tile: out through the idle stage ring and TMA stores
-        tail_store_f32_planes<BN>(tm, smem + q * 32768, lane, b1, true, &tmYh, &tmYl, n0, m0 + q * 32,
-                                  m0 + q * 32 < M);
+        // the CTA's last tile: out through the idle stage ring and TMA stores, the
+        // quarter's column blocks shared with its four producer warps (worker 0 of 5)
+        tail_store_f32_planes<BN, 1>(tm, smem + (q * 5) * 8192, lane, b1, true, &tmYh, &tmYl, n0, m0 + q * 32,
+                                     m0 + q * 32 < M, 0, 5);
         tc_fence_before();
         mbar_arrive(&acc_empty[buf]);
         continue;
@@ -195,31 +196,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---- producers: layer 0 for row pr of the tile, 32 columns per k-block, written
     // as the A tiles' hi/lo planes (row pr: 8 chunks of 16 B, chunk c at slot c ^ (pr % 8))
-    {
-      // layer 0's weights into rows of 16 -- weights, the bias (slot K0), zeros -- with
-      // every load in flight before the first store; then wait for the producers only
-      const int pt = threadIdx.x - 192;
-      constexpr int kPer = kW0Max * kKM / kProducers;
-      static_assert(kW0Max * kKM % kProducers == 0, "weight staging split");
-      float w[kPer];
-#pragma unroll
-      for (int i = 0; i < kPer; ++i) {
-        const int e = pt + i * kProducers, j = e / kKM, k = e % kKM;
-        w[i] = j >= N0 ? 0.f : k < K0 ? __ldg(W0 + j * K0 + k) : k == K0 ? __ldg(b0 + j) : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < kPer; ++i)
-        if (pt + i * kProducers < N0 * kKM) sW0[pt + i * kProducers] = w[i];
-      named_barrier_sync(1, kProducers);
-    }
     const int pr = ((warp - 6) & 3) * 32 + lane;
     const int c0 = ((warp - 6) >> 2) * (8 / kGroups);
-    const uint32_t rbase = static_cast<uint32_t>((pr >> 3) * 1024 + (pr & 7) * 128);
-    uint32_t g = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    // the row's dense features, padded: x[K0] = 1 multiplies the bias, the rest 0
+    float x[kKM];
+    auto load_x = [&](int t) {
       const int row = (t / NT) * kBM + pr;
-      float x[kKM];
 #pragma unroll
       for (int k = 0; k < kKM; ++k) x[k] = k == K0 ? 1.f : 0.f;
       if (row < M) {
@@ -229,6 +211,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < kKM; ++k)
           if (k < K0) x[k] = __ldg(dense + k);
       }
+    };
+    if (static_cast<int>(blockIdx.x) < tiles) load_x(blockIdx.x);  // in flight during the staging
+    {
+      // layer 0's weights into rows of 16 -- weights, the bias (slot K0), zeros -- with
+      // every load in flight before the first store; then wait for the producers only
+      const int pt = threadIdx.x - 192;
+      // W0 is [N0, K0] contiguous and 16-byte aligned: kV float4 per thread cover it,
+      // then the biases (N0 / 4 float4) and the zero padding
+      constexpr int kV = (kW0Max * (kKM - 1) / 4 + kProducers - 1) / kProducers;
+      const int nv = N0 * K0 / 4;  // N0 is a multiple of 32, so N0 * K0 is a multiple of 4
+      float4 wv[kV];
+#pragma unroll
+      for (int i = 0; i < kV; ++i)
+        wv[i] = pt + i * kProducers < nv ? __ldg(reinterpret_cast<const float4*>(W0) + pt + i * kProducers)
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 bv = pt < N0 / 4 ? __ldg(reinterpret_cast<const float4*>(b0) + pt) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < kV; ++i) {
+        const int e4 = pt + i * kProducers;
+        if (e4 < nv) {
+          const float f[4] = {wv[i].x, wv[i].y, wv[i].z, wv[i].w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = 4 * e4 + u;
+            sW0[(e / K0) * kKM + e % K0] = f[u];
+          }
+        }
+      }
+      if (pt < N0 / 4) {
+        const float f[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sW0[(4 * pt + u) * kKM + K0] = f[u];
+      }
+      for (int e = pt; e < N0 * (kKM - 1 - K0); e += kProducers)
+        sW0[(e / (kKM - 1 - K0)) * kKM + K0 + 1 + e % (kKM - 1 - K0)] = 0.f;
+      named_barrier_sync(1, kProducers);
+    }
+    const uint32_t rbase = static_cast<uint32_t>((pr >> 3) * 1024 + (pr & 7) * 128);
+    uint32_t g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      if (t != static_cast<int>(blockIdx.x)) load_x(t);
       for (int kb = 0; kb < KB; ++kb, ++g) {
         const int s = g % NST;
         const uint32_t ph = (g / NST) & 1;
@@ -264,6 +288,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         fence_proxy_async_smem();  // generic-proxy writes -> the tensor cores' reads
         mbar_arrive(&full[s]);
+      }
+      if (ok && t + static_cast<int>(gridDim.x) >= tiles) {
+        // the CTA's last tile: help the epilogue warp of this row quarter write it
+        // (worker 1 + set of 5), once its MMAs have completed
+        const int q = warp & 3, wk = 1 + ((warp - 6) >> 2);
+        const int i = (t - static_cast<int>(blockIdx.x)) / static_cast<int>(gridDim.x);
+        const int buf = i & 1;
+        const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+        if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
+        tc_fence_after();
+        const uint32_t tm = tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16);
+        tail_store_f32_planes<BN, 1>(tm, smem + (q * 5 + wk) * 8192, lane, b1, true, &tmYh, &tmYl, n0,
+                                     m0 + q * 32, m0 + q * 32 < M, wk, 5);
       }
     }
   }
@@ -333,7 +370,7 @@ cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float
   if (tab.M <= 0) return cudaSuccess;
   if (!bottom01_fusable(K0, N0, N1) || (ldy % 4)) return cudaErrorInvalidValue;
   for (const void* p : {static_cast<const void*>(w1h), static_cast<const void*>(w1l), static_cast<const void*>(yh),
-                        static_cast<const void*>(yl)})
+                        static_cast<const void*>(yl), static_cast<const void*>(W0), static_cast<const void*>(b0)})
     if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
   if (cfg.bn == 0) cfg = bottom01_default(N1);
   if (N1 % cfg.bn) return cudaErrorInvalidValue;

@@ -339,25 +339,28 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // is idle, so each epilogue warp stages its 32 rows x 32 columns there (128-byte
 // swizzle: row r's 16-byte chunk j at r * 128 + ((j ^ r % 8) * 16), conflict-free)
 // and writes them with TMA stores: whole 128-byte row pieces instead of a 16-byte
-// piece of 32 different rows per store instruction.  `stg` is the warp's 32 KB
-// (four hi/lo buffer pairs, 1024-byte aligned); `tm` its TMEM lanes at column 0;
-// (x0, y0) the block's first column and row in the output; `live` false when all
-// 32 rows lie beyond the output (nothing is stored).  Same arithmetic as the
-// direct stores, so the same bits.
-template <int BN>
+// piece of 32 different rows per store instruction.  The warp handles column
+// blocks first, first + step, ... (32 columns each) of its 32 rows, so several
+// warps can share one row quarter.  `stg` is the warp's NP hi/lo buffer pairs
+// (8 KB each, 1024-byte aligned); `tm` its TMEM lanes at column 0; (x0, y0) the
+// tile's first column and the quarter's first row in the output; `live` false
+// when all 32 rows lie beyond the output (nothing is stored).  Same arithmetic as
+// the direct stores, so the same bits.
+template <int BN, int NP>
 __device__ __forceinline__ void tail_store_f32_planes(uint32_t tm, uint8_t* stg, int lane,
                                                       const float* __restrict__ bias, bool relu,
                                                       const void* tmYh, const void* tmYl, int x0, int y0,
-                                                      bool live) {
+                                                      bool live, int first = 0, int step = 1) {
+  int it = 0;
 #pragma unroll 1
-  for (int c0 = 0; c0 < BN; c0 += 32) {
+  for (int c0 = 32 * first; c0 < BN; c0 += 32 * step, ++it) {
     uint32_t v[32];
     tmem_ld_32cols(tm + c0, v);
     tmem_ld_wait();
-    uint8_t* hb = stg + ((c0 / 32) & 3) * 8192;
+    uint8_t* hb = stg + (it % NP) * 8192;
     uint8_t* lb = hb + 4096;
-    if (c0 >= 128) {
-      if (lane == 0) tma_store_wait_read<3>();  // this pair's stores of four blocks ago
+    if (it >= NP) {
+      if (lane == 0) tma_store_wait_read<NP - 1>();  // this pair's stores of NP blocks ago
       __syncwarp();
     }
 #pragma unroll

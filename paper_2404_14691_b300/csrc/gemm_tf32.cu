@@ -461,7 +461,7 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
       }
       if (t + static_cast<int>(gridDim.x) >= tiles) {
         // the CTA's last tile: out through the idle stage ring and TMA stores
-        tail_store_f32_planes<BN>(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16),
+        tail_store_f32_planes<BN, 4>(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16),
                                   smem + q * 32768, lane, bias, relu != 0, tmYh, tmYl, n0, m0 + q * 32,
                                   m0 + q * 32 < M);
         tc_fence_before();
