@@ -40,13 +40,28 @@ struct B01Cfg {
   static_assert(NST * STAGE >= 20 * 8192, "last-tile output staging: 8 KB per epilogue and producer warp");
 };
 
-template <int BN, int NST>
+// Layer 2 of the bottom MLP, when the kernel also computes it (N2 outputs from
+// layer 1's BN = N1 outputs): its weight planes and bias.
+struct Layer2 {
+  CUtensorMap wh, wl;  // W2 hi / lo planes, [N2, N1]
+  const float* b;      // [N2]
+  int n;               // N2
+};
+
+// L2: the kernel also computes layer 2.  Every CTA then owns one tile whose rows are
+// complete (BN = N1), so after layer 1's MMAs the whole stage ring is free for
+// layer 2: rounds of up to h k-blocks, each a 128 x 32 block of ReLU(acc1 + b1)
+// written as hi/lo A tiles by the 20 worker warps (epilogue and producer warps)
+// and the matching W2 planes loaded by TMA, three tf32 MMAs per k-step into a
+// second accumulator (TMEM columns BN..BN+N2).  Layer 1's output is never stored;
+// `tmYh` / `tmYl` then describe layer 2's output.
+template <int BN, int NST, bool L2>
 __global__ void __launch_bounds__(kThreads, 1)
     bottom01_kernel(const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                     const __grid_constant__ CUtensorMap tmYh, const __grid_constant__ CUtensorMap tmYl,
                     const __grid_constant__ InvTable tab, int K0, int N0, const float* __restrict__ W0,
                     const float* __restrict__ b0, int N1, const float* __restrict__ b1, float* __restrict__ Yh,
-                    float* __restrict__ Yl, int ldy, int* err) {
+                    float* __restrict__ Yl, int ldy, int* err, const __grid_constant__ Layer2 l2) {
   using C = B01Cfg<BN, NST>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = smem_align1024(smem_raw);
@@ -59,7 +74,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty = full + NST;
   uint64_t* acc_full = empty + NST;  // [2]
   uint64_t* acc_empty = acc_full + 2;  // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* w2full = acc_empty + 2;    // layer 2: W2 planes of a round loaded
+  uint64_t* a2full = w2full + 1;       // layer 2: A tiles of a round written
+  uint64_t* l2done = a2full + 1;       // layer 2: a round's MMAs complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(l2done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int M = tab.M;
@@ -77,6 +95,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 128);
     }
+    mbar_init(w2full, 1);
+    mbar_init(a2full, 20 * 32);  // every epilogue and producer thread, once per round
+    mbar_init(l2done, 1);
     fence_mbar_init();
   }
   if (warp == 2 && lane == 0) {
@@ -84,6 +105,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tma_prefetch_desc(&tmBl);
     tma_prefetch_desc(&tmYh);
     tma_prefetch_desc(&tmYl);
+    if (L2) {
+      tma_prefetch_desc(&l2.wh);
+      tma_prefetch_desc(&l2.wl);
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -143,10 +168,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp < 6) {
-    // ---- epilogue warps: layer 1's bias, ReLU, hi/lo planes
+    // ---- epilogue warps: layer 1's bias, ReLU, hi/lo planes (with L2, the layer-2
+    // phase below consumes the accumulator instead)
     const int q = warp & 3;
     int i = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+    for (int t = blockIdx.x; t < (L2 ? 0 : tiles); t += gridDim.x, ++i) {
       const int buf = i & 1;
       const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
       if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
@@ -289,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async_smem();  // generic-proxy writes -> the tensor cores' reads
         mbar_arrive(&full[s]);
       }
-      if (ok && t + static_cast<int>(gridDim.x) >= tiles) {
+      if (!L2 && ok && t + static_cast<int>(gridDim.x) >= tiles) {
         // the CTA's last tile: help the epilogue warp of this row quarter write it
         // (worker 1 + set of 5), once its MMAs have completed
         const int q = warp & 3, wk = 1 + ((warp - 6) >> 2);
@@ -304,6 +330,105 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   }
+  if constexpr (L2) {
+    if (static_cast<int>(blockIdx.x) < tiles) {
+      const int N2 = l2.n;
+      constexpr int KB2 = BN / kBK;  // layer 2 reduces over layer 1's BN = N1 outputs
+      const int w2kb = N2 * kBK * 4;  // one plane of a W2 k-block
+      const int h = min(KB2, (NST * C::STAGE) / (2 * C::A_BYTES + 2 * w2kb));
+      const int R = (KB2 + h - 1) / h;
+      uint8_t* a2 = smem;                         // h slots: A hi, A lo (16 KB each)
+      uint8_t* w2 = smem + h * 2 * C::A_BYTES;  // h slots: W2 hi, W2 lo
+      const int m0 = blockIdx.x * kBM;
+      bool ok = true;
+      if (warp == 0) {
+        if (lane == 0) {
+          // the W2 slots overlap the stage ring: wait until layer 1's MMAs have read it
+          ok = mbar_wait(&acc_full[0], 0, err);
+          for (int r = 0; r < R && ok; ++r) {
+            if (r > 0 && !mbar_wait(l2done, (r - 1) & 1, err)) break;  // the previous round's reads
+            const int k0 = r * h, k1 = min(KB2, k0 + h);
+            mbar_arrive_expect_tx(w2full, static_cast<uint32_t>((k1 - k0) * 2 * w2kb));
+            for (int kb = k0; kb < k1; ++kb) {
+              uint8_t* dst = w2 + (kb - k0) * 2 * w2kb;
+              tma_load_2d(dst, &l2.wh, kb * kBK, 0, w2full);
+              tma_load_2d(dst + w2kb, &l2.wl, kb * kBK, 0, w2full);
+            }
+          }
+        }
+      } else if (warp == 1) {
+        if (lane == 0) {
+          const uint32_t idesc2 = idesc_tf32_f32(kBM, N2);
+          const uint32_t acc2 = tmem + BN;
+          for (int r = 0; r < R && ok; ++r) {
+            if (!mbar_wait(w2full, r & 1, err) || !mbar_wait(a2full, r & 1, err)) break;
+            tc_fence_after();
+            const int k0 = r * h, k1 = min(KB2, k0 + h);
+            for (int kb = k0; kb < k1; ++kb) {
+              const uint32_t ah = smem_u32(a2 + (kb - k0) * 2 * C::A_BYTES), al = ah + C::A_BYTES;
+              const uint32_t bh = smem_u32(w2 + (kb - k0) * 2 * w2kb), bl = bh + w2kb;
+#pragma unroll
+              for (int k = 0; k < kBK / 8; ++k) {
+                const uint32_t o = k * 32;
+                tc_mma_tf32(acc2, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc2,
+                            (kb | k) != 0 ? 1u : 0u);
+                tc_mma_tf32(acc2, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc2, 1u);
+                tc_mma_tf32(acc2, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc2, 1u);
+              }
+            }
+            tc_commit(l2done);
+          }
+        }
+      } else {
+        // workers: per row quarter q the epilogue warp (wk 0) and four producer warps
+        // (wk 1..4) share the 32-column blocks, as in the last-tile output above
+        const int q = warp & 3, wk = warp < 6 ? 0 : 1 + ((warp - 6) >> 2);
+        const uint32_t lanes = static_cast<uint32_t>(q * 32) << 16;
+        const int ar = q * 32 + lane;  // this thread's row of the A tiles
+        ok = mbar_wait(&acc_full[0], 0, err);
+        tc_fence_after();
+        for (int r = 0; r < R && ok; ++r) {
+          if (r > 0 && !mbar_wait(l2done, (r - 1) & 1, err)) {
+            ok = false;
+            break;
+          }
+          const int k0 = r * h, k1 = min(KB2, k0 + h);
+          for (int kb = k0 + wk; kb < k1; kb += 5) {
+            uint32_t v[32];
+            tmem_ld_32cols(tmem + lanes + kb * kBK, v);
+            tmem_ld_wait();
+            uint8_t* ah = a2 + (kb - k0) * 2 * C::A_BYTES;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              float o[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) o[u] = fmaxf(__uint_as_float(v[4 * j + u]) + __ldg(b1 + kb * kBK + 4 * j + u), 0.f);
+              float4 hv, lv;
+              hv.x = to_tf32_rna(o[0]);
+              hv.y = to_tf32_rna(o[1]);
+              hv.z = to_tf32_rna(o[2]);
+              hv.w = to_tf32_rna(o[3]);
+              lv.x = o[0] - hv.x;
+              lv.y = o[1] - hv.y;
+              lv.z = o[2] - hv.z;
+              lv.w = o[3] - hv.w;
+              const uint32_t off = static_cast<uint32_t>(ar * 128 + ((j ^ (ar & 7)) << 4));
+              *reinterpret_cast<float4*>(ah + off) = hv;
+              *reinterpret_cast<float4*>(ah + C::A_BYTES + off) = lv;
+            }
+          }
+          fence_proxy_async_smem();
+          mbar_arrive(a2full);
+        }
+        // layer 2's output (bias, ReLU, hi/lo planes) once the last round's MMAs completed
+        if (ok && mbar_wait(l2done, (R - 1) & 1, err)) {
+          tc_fence_after();
+          tail_store_f32_planes<256, 1>(tmem + BN + lanes, smem + (q * 5 + wk) * 8192, lane, l2.b, true, &tmYh,
+                                        &tmYl, 0, m0 + q * 32, m0 + q * 32 < M, wk, 5, N2);
+        }
+      }
+    }
+  }
   __syncwarp();
   tc_fence_before();
   __syncthreads();
@@ -312,13 +437,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 int g_sms_b01 = 0;
 
-template <int BN, int NST>
+// yh / yl / ldy: layer 1's output, or layer 2's when `w2h` is given (N2 outputs).
+template <int BN, int NST, bool L2>
 cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
                        const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy, int* err,
-                       cudaStream_t s) {
+                       cudaStream_t s, const float* w2h, const float* w2l, const float* b2, int N2) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(bottom01_kernel<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(bottom01_kernel<BN, NST, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          B01Cfg<BN, NST>::SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -328,14 +454,23 @@ cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, con
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms_b01, cudaDevAttrMultiProcessorCount, dev);
   }
+  const int nout = L2 ? N2 : N1;
   CUtensorMap tbh, tbl, tyh, tyl;
+  Layer2 l2{};
   if (!make_tmap_2d(&tbh, 0, w1h, N1, N0, N0, kBK, BN) || !make_tmap_2d(&tbl, 0, w1l, N1, N0, N0, kBK, BN) ||
-      !make_tmap_2d(&tyh, 0, yh, tab.M, N1, ldy, 32, 32) || !make_tmap_2d(&tyl, 0, yl, tab.M, N1, ldy, 32, 32))
+      !make_tmap_2d(&tyh, 0, yh, tab.M, nout, ldy, 32, 32) || !make_tmap_2d(&tyl, 0, yl, tab.M, nout, ldy, 32, 32))
     return cudaErrorInvalidValue;
   const int tiles = (N1 / BN) * ((tab.M + kBM - 1) / kBM);
+  if (L2) {
+    if (BN != N1 || tiles > g_sms_b01) return cudaErrorInvalidValue;  // one whole-row tile per CTA
+    if (!make_tmap_2d(&l2.wh, 0, w2h, N2, N1, N1, kBK, N2) || !make_tmap_2d(&l2.wl, 0, w2l, N2, N1, N1, kBK, N2))
+      return cudaErrorInvalidValue;
+    l2.b = b2;
+    l2.n = N2;
+  }
   const int grid = tiles < g_sms_b01 ? tiles : g_sms_b01;
-  bottom01_kernel<BN, NST><<<grid, kThreads, B01Cfg<BN, NST>::SMEM, s>>>(tbh, tbl, tyh, tyl, tab, K0, N0, W0, b0, N1, b1, yh, yl,
-                                                                     ldy, err);
+  bottom01_kernel<BN, NST, L2><<<grid, kThreads, B01Cfg<BN, NST>::SMEM, s>>>(
+      tbh, tbl, tyh, tyl, tab, K0, N0, W0, b0, N1, b1, yh, yl, ldy, err, l2);
   count_launch();
   return cudaGetLastError();
 }
@@ -348,7 +483,8 @@ bool bottom01_fusable(int K0, int N0, int N1) {
 
 // Tile configurations: (BN, stages + 100), all persistent; BN = N1 computes layer 0
 // once per row, narrower tiles recompute it for each of the N1 / BN column tiles.
-const GemmCfg kB01Cfgs[] = {{256, 102}, {128, 103}, {64, 104}};
+// (256, 202): the same tile, and layer 2 computed in the kernel too.
+const GemmCfg kB01Cfgs[] = {{256, 102}, {128, 103}, {64, 104}, {256, 202}};
 
 int bottom01_candidates(GemmCfg* out, int max) {
   int n = 0;
@@ -356,6 +492,15 @@ int bottom01_candidates(GemmCfg* out, int max) {
     if (n < max) out[n++] = c;
   if (n < max) out[n++] = GemmCfg{1, 1};  // separate kernels
   return n;
+}
+
+bool bottom012_fusable(int N1, int N2, int M) {
+  if (!g_sms_b01) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms_b01, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return N1 == 256 && N2 >= 32 && N2 <= 256 && N2 % 32 == 0 && (M + kBM - 1) / kBM <= g_sms_b01;
 }
 
 GemmCfg bottom01_default(int N1) {
@@ -366,28 +511,40 @@ GemmCfg bottom01_default(int N1) {
 
 cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
                                 const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy,
-                                int* err, cudaStream_t s, GemmCfg cfg) {
+                                int* err, cudaStream_t s, GemmCfg cfg, const float* w2h, const float* w2l,
+                                const float* b2, int N2, int* layers) {
+  const bool three = w2h && w2l && b2 && bottom012_fusable(N1, N2, tab.M);
+  if (cfg.bn == 0) cfg = three ? GemmCfg{256, 202} : bottom01_default(N1);
+  if (cfg.stages == 202 && !three) cfg = GemmCfg{256, 102};  // layer 2 then runs separately
+  if (layers) *layers = cfg.stages == 202 ? 3 : 2;
   if (tab.M <= 0) return cudaSuccess;
   if (!bottom01_fusable(K0, N0, N1) || (ldy % 4)) return cudaErrorInvalidValue;
   for (const void* p : {static_cast<const void*>(w1h), static_cast<const void*>(w1l), static_cast<const void*>(yh),
-                        static_cast<const void*>(yl), static_cast<const void*>(W0), static_cast<const void*>(b0)})
+                        static_cast<const void*>(yl), static_cast<const void*>(W0), static_cast<const void*>(b0),
+                        static_cast<const void*>(w2h), static_cast<const void*>(w2l)})
     if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
-  if (cfg.bn == 0) cfg = bottom01_default(N1);
   if (N1 % cfg.bn) return cudaErrorInvalidValue;
+  if (cfg.bn == 256 && cfg.stages == 202) {
+    return launch_b01<256, 2, true>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s, w2h, w2l, b2, N2);
+  }
   if (cfg.bn == 256 && cfg.stages == 102)
-    return launch_b01<256, 2>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s);
+    return launch_b01<256, 2, false>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s, nullptr, nullptr,
+                                     nullptr, 0);
   if (cfg.bn == 128 && cfg.stages == 103)
-    return launch_b01<128, 3>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s);
+    return launch_b01<128, 3, false>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s, nullptr, nullptr,
+                                     nullptr, 0);
   if (cfg.bn == 64 && cfg.stages == 104)
-    return launch_b01<64, 4>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s);
+    return launch_b01<64, 4, false>(tab, K0, N0, W0, b0, N1, w1h, w1l, b1, yh, yl, ldy, err, s, nullptr, nullptr,
+                                    nullptr, 0);
   return cudaErrorInvalidValue;
 }
 
 void preload_bottom01_kernels() {
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, bottom01_kernel<256, 2>);
-  cudaFuncGetAttributes(&fa, bottom01_kernel<128, 3>);
-  cudaFuncGetAttributes(&fa, bottom01_kernel<64, 4>);
+  cudaFuncGetAttributes(&fa, bottom01_kernel<256, 2, false>);
+  cudaFuncGetAttributes(&fa, bottom01_kernel<256, 2, true>);
+  cudaFuncGetAttributes(&fa, bottom01_kernel<128, 3, false>);
+  cudaFuncGetAttributes(&fa, bottom01_kernel<64, 4, false>);
 }
 
 }  // namespace sage

@@ -344,16 +344,17 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 // warps can share one row quarter.  `stg` is the warp's NP hi/lo buffer pairs
 // (8 KB each, 1024-byte aligned); `tm` its TMEM lanes at column 0; (x0, y0) the
 // tile's first column and the quarter's first row in the output; `live` false
-// when all 32 rows lie beyond the output (nothing is stored).  Same arithmetic as
-// the direct stores, so the same bits.
+// when all 32 rows lie beyond the output (nothing is stored); `ncols` (<= BN, a
+// multiple of 32) the tile's width.  Same arithmetic as the direct stores, so the
+// same bits.
 template <int BN, int NP>
 __device__ __forceinline__ void tail_store_f32_planes(uint32_t tm, uint8_t* stg, int lane,
                                                       const float* __restrict__ bias, bool relu,
                                                       const void* tmYh, const void* tmYl, int x0, int y0,
-                                                      bool live, int first = 0, int step = 1) {
+                                                      bool live, int first = 0, int step = 1, int ncols = BN) {
   int it = 0;
 #pragma unroll 1
-  for (int c0 = 32 * first; c0 < BN; c0 += 32 * step, ++it) {
+  for (int c0 = 32 * first; c0 < ncols; c0 += 32 * step, ++it) {
     uint32_t v[32];
     tmem_ld_32cols(tm + c0, v);
     tmem_ld_wait();

@@ -68,8 +68,9 @@ int tf32_presplit_candidates(GemmCfg* out, int max);
 GemmCfg tuned_gemm(int kind, int M, int N, int K);
 // Times every configuration of one shape and records the fastest.
 sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg* chosen, double* best_ms);
-// Fused bottom layers 0 and 1 against the separate kernels (kBottom01).
-sage_status autotune_bottom01(int M, int K0, int N0, int N1, cudaStream_t s, GemmCfg* chosen);
+// Fused bottom layers 0 and 1 (and 2, when N2 > 0 and the shape allows) against the
+// separate kernels (kBottom01).
+sage_status autotune_bottom01(int M, int K0, int N0, int N1, int N2, cudaStream_t s, GemmCfg* chosen);
 
 // Dense layers y = act(x W^T + b).
 cudaError_t launch_linear_f32(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias,
@@ -97,15 +98,22 @@ cudaError_t launch_linear_bf16_tc_head(int M, int N, int K, const void* x, int l
                                        const HeadParams& hp);
 // Bottom layers 0 and 1 of a pre-split fp32 function in one kernel: layer 0
 // (K0 <= 15 dense inputs, N0 outputs, ReLU) is computed into layer 1's shared-memory
-// A tiles; layer 1's output (N1 columns, ReLU) is written as hi/lo planes.  Same bits
-// as launch_bottom0 followed by launch_linear_f32_tc_presplit.  cfg: one of
-// bottom01_candidates' fused configurations, or {0, 0} for bottom01_default.
+// A tiles; layer 1's output (N1 columns, ReLU) is written as hi/lo planes.  With
+// layer 2's weight planes and bias (N2 outputs) and configuration (256, 202) -- or
+// {0, 0} when bottom012_fusable -- the kernel computes layer 2 as well and writes
+// only its output (yh / yl / ldy then describe layer 2's output); *layers reports 2
+// or 3.  Same bits as launch_bottom0 followed by launch_linear_f32_tc_presplit per
+// layer.  cfg: one of bottom01_candidates' fused configurations, or {0, 0}.
 bool bottom01_fusable(int K0, int N0, int N1);
+// Layer 2 too: N1 = 256, N2 a multiple of 32 up to 256, one 128-row tile per SM.
+bool bottom012_fusable(int N1, int N2, int M);
 int bottom01_candidates(GemmCfg* out, int max);  // the last one, {1, 1}, means separate kernels
 GemmCfg bottom01_default(int N1);
 cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
                                 const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy,
-                                int* err, cudaStream_t s, GemmCfg cfg);
+                                int* err, cudaStream_t s, GemmCfg cfg, const float* w2h = nullptr,
+                                const float* w2l = nullptr, const float* b2 = nullptr, int N2 = 0,
+                                int* layers = nullptr);
 // hi[i] = tf32(src[i]) (round to nearest), lo[i] = src[i] - hi[i].
 cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s);
 // fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.

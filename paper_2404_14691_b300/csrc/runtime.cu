@@ -852,19 +852,29 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   if (overlap) stream = s.branch;
   // bottom MLP (layer 0 reads each invocation's dense rows); on the pre-split fp32
   // path layers 0 and 1 run as one kernel unless the tuning table says otherwise
+  // (and layer 2 too, when the shape allows one whole-row tile per SM)
   int l1 = 1;
   if (ps2 && nb >= 2 && bottom01_fusable(e->layers[0].in, e->layers[0].out, e->layers[1].out)) {
     const Layer& L0 = e->layers[0];
     const Layer& L1 = e->layers[1];
     const GemmCfg c = tuned_gemm(kBottom01, M, L1.out, L1.in);
     if (c.bn != 1) {
-      void* y = nb == 2 ? bot_out : s.bot[1];
-      const int ldy = nb == 2 ? cd : e->bot[1];
-      ProfScope ps(stream, kProfBottom01, 2.0 * M * (L0.in * L0.out + L1.in * L1.out));
+      const bool three = nb >= 3 && (c.bn == 0 || c.stages == 202) &&
+                         bottom012_fusable(L1.out, e->layers[2].out, M);
+      const int last = three ? 2 : 1;
+      void* y = last == nb - 1 ? bot_out : s.bot[last];
+      const int ldy = last == nb - 1 ? cd : e->bot[last];
+      double flops = 2.0 * M * (L0.in * L0.out + L1.in * L1.out);
+      if (three) flops += 2.0 * M * e->layers[2].in * e->layers[2].out;
+      ProfScope ps(stream, kProfBottom01, flops);
+      int done = 0;
       SAGE_CK(launch_bottom01_f32(tab, L0.in, L0.out, static_cast<const float*>(L0.W), L0.b, L1.out,
                                   e->wplanes[1].first, e->wplanes[1].second, L1.b, static_cast<float*>(y),
-                                  lo_of(y, ldy), ldy, e->d_err, stream, c));
-      l1 = 2;
+                                  lo_of(y, ldy), ldy, e->d_err, stream, three ? GemmCfg{256, 202} : c,
+                                  three ? e->wplanes[2].first : nullptr, three ? e->wplanes[2].second : nullptr,
+                                  three ? e->layers[2].b : nullptr, three ? e->layers[2].out : 0, &done));
+      if (done != last + 1) return fail(SAGE_ERR_CUDA, "fused bottom kernel ran %d layers, expected %d", done, last + 1);
+      l1 = last + 1;
     }
   }
   if (l1 == 1) {
@@ -1715,7 +1725,8 @@ sage_status sage_autotune(sage_fn f, int rows, void* stream) {
     if (st != SAGE_OK) return st;
   }
   if (e->presplit && nb >= 2 && bottom01_fusable(e->layers[0].in, e->layers[0].out, e->layers[1].out))
-    return autotune_bottom01(rows, e->layers[0].in, e->layers[0].out, e->layers[1].out, s, nullptr);
+    return autotune_bottom01(rows, e->layers[0].in, e->layers[0].out, e->layers[1].out,
+                             nb >= 3 ? e->layers[2].out : 0, s, nullptr);
   return SAGE_OK;
 }
 

@@ -134,16 +134,22 @@ sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg
   return SAGE_OK;
 }
 
-// Bottom layers 0 and 1 of a pre-split fp32 function (K0 dense inputs, N0 and N1
-// outputs): times the fused kernel's tiles against bottom0 followed by layer 1's
-// GEMM at its own tuned tile (so tune that GEMM first) and records the fastest
-// under (kBottom01, M bucket, N1, N0); {1, 1} records that separate kernels won.
-sage_status autotune_bottom01(int M, int K0, int N0, int N1, cudaStream_t s, GemmCfg* chosen) {
+// Bottom layers 0 and 1 (and 2 when N2 > 0) of a pre-split fp32 function (K0 dense
+// inputs, N0, N1 and N2 outputs): times the fused kernel's tiles against bottom0
+// followed by the layer GEMMs at their own tuned tiles (so tune those first); when
+// N2 > 0 every candidate includes layer 2 -- its GEMM, or the three-layer kernel
+// (256, 202) where the shape allows it.  Records the fastest under (kBottom01,
+// M bucket, N1, N0); {1, 1} records that separate kernels won.
+sage_status autotune_bottom01(int M, int K0, int N0, int N1, int N2, cudaStream_t s, GemmCfg* chosen) {
   if (!bottom01_fusable(K0, N0, N1)) return set_last_error("autotune: shape cannot fuse"), SAGE_ERR_INVALID;
   const int Mb = bucket(M);
-  const size_t sizes[] = {static_cast<size_t>(Mb) * K0, static_cast<size_t>(N0) * K0, static_cast<size_t>(N0),
-                          static_cast<size_t>(N1) * N0, static_cast<size_t>(N1), 2 * static_cast<size_t>(Mb) * N0,
-                          2 * static_cast<size_t>(Mb) * N1, 64};
+  const int n2 = N2 > 0 ? N2 : 0;
+  const size_t sizes[] = {static_cast<size_t>(Mb) * K0,     static_cast<size_t>(N0) * K0,
+                          static_cast<size_t>(N0),          static_cast<size_t>(N1) * N0,
+                          static_cast<size_t>(N1),          2 * static_cast<size_t>(Mb) * N0,
+                          2 * static_cast<size_t>(Mb) * N1, static_cast<size_t>(n2 ? n2 : 1) * N1,
+                          static_cast<size_t>(n2 ? n2 : 1), 2 * static_cast<size_t>(Mb) * (n2 ? n2 : 1),
+                          64};
   constexpr int kBufs = sizeof(sizes) / sizeof(sizes[0]);
   float* b[kBufs] = {};
   auto cleanup = [&] {
@@ -158,12 +164,20 @@ sage_status autotune_bottom01(int M, int K0, int N0, int N1, cudaStream_t s, Gem
     cudaMemsetAsync(b[i], i == kBufs - 1 ? 0 : 0x3c, sizes[i] * 4, s);
   }
   float *dense = b[0], *w0 = b[1], *b0 = b[2], *w1 = b[3], *b1 = b[4], *y0 = b[5], *y1 = b[6];
-  int* err = reinterpret_cast<int*>(b[7]);
+  float *w2 = b[7], *b2 = b[8], *y2 = b[9];
+  int* err = reinterpret_cast<int*>(b[10]);
   std::unique_ptr<InvTable> tab(new InvTable());
   tab->n = 1;
   tab->M = Mb;
   tab->d[0] = InvDesc{dense, nullptr, nullptr, nullptr, Mb, 0, 0};
   const GemmCfg g1 = tuned_gemm(kGemmTf32Pre, Mb, N1, N0);
+  const GemmCfg g2 = n2 ? tuned_gemm(kGemmTf32Pre, Mb, n2, N1) : GemmCfg{0, 0};
+  float* y1l = y1 + static_cast<size_t>(Mb) * N1;
+  float* y2l = y2 + static_cast<size_t>(Mb) * (n2 ? n2 : 1);
+  auto layer2 = [&]() -> cudaError_t {
+    if (!n2) return cudaSuccess;
+    return launch_linear_f32_tc_presplit(Mb, n2, N1, y1, y1l, N1, w2, w2, b2, 1, y2, y2l, n2, err, s, g2);
+  };
   GemmCfg cands[16];
   const int nc = bottom01_candidates(cands, 16);
   cudaEvent_t e0, e1;
@@ -173,15 +187,22 @@ sage_status autotune_bottom01(int M, int K0, int N0, int N1, cudaStream_t s, Gem
   float best_t = 1e30f;
   for (int c = 0; c < nc; ++c) {
     if (N1 % cands[c].bn) continue;
+    const bool three = cands[c].stages == 202;
+    if (three && !(n2 && bottom012_fusable(N1, n2, Mb))) continue;
     auto run = [&]() -> cudaError_t {
+      cudaError_t ce;
       if (cands[c].bn == 1) {
-        cudaError_t ce = launch_bottom0(0, *tab, K0, N0, w0, b0, y0, N0, s, y0 + static_cast<size_t>(Mb) * N0);
+        ce = launch_bottom0(0, *tab, K0, N0, w0, b0, y0, N0, s, y0 + static_cast<size_t>(Mb) * N0);
         if (ce != cudaSuccess) return ce;
-        return launch_linear_f32_tc_presplit(Mb, N1, N0, y0, y0 + static_cast<size_t>(Mb) * N0, N0, w1, w1, b1, 1,
-                                             y1, y1 + static_cast<size_t>(Mb) * N1, N1, err, s, g1);
+        ce = launch_linear_f32_tc_presplit(Mb, N1, N0, y0, y0 + static_cast<size_t>(Mb) * N0, N0, w1, w1, b1, 1, y1,
+                                           y1l, N1, err, s, g1);
+        return ce != cudaSuccess ? ce : layer2();
       }
-      return launch_bottom01_f32(*tab, K0, N0, w0, b0, N1, w1, w1, b1, y1, y1 + static_cast<size_t>(Mb) * N1, N1,
-                                 err, s, cands[c]);
+      if (three)
+        return launch_bottom01_f32(*tab, K0, N0, w0, b0, N1, w1, w1, b1, y2, y2l, n2, err, s, cands[c], w2, w2, b2,
+                                   n2);
+      ce = launch_bottom01_f32(*tab, K0, N0, w0, b0, N1, w1, w1, b1, y1, y1l, N1, err, s, cands[c]);
+      return ce != cudaSuccess ? ce : layer2();
     };
     if (run() != cudaSuccess) {
       cudaGetLastError();
