@@ -316,6 +316,18 @@ def check_close(got, ref, mag, rtol: float) -> dict:
             "worst_index": worst}
 
 
+def check_output(got, ref, mag, rtol: float) -> dict:
+    """The function's final outputs (sigmoids, in (0, 1)): the componentwise bound of
+    check_close and, in addition, the plain relative error |got - ref| <= rtol * |ref|
+    of every output, the tolerance read literally."""
+    c = check_close(got, ref, mag, rtol)
+    err = np.abs(np.asarray(got, dtype=np.float64) - np.asarray(ref, dtype=np.float64))
+    plain_ok = err <= rtol * np.abs(np.asarray(ref, dtype=np.float64))
+    c["n_bad_plain"] = int((~plain_ok).sum())
+    c["ok"] = c["ok"] and bool(plain_ok.all())
+    return c
+
+
 # ---------------------------------------------------------------- setup-time model
 
 def setup_latency_model(stages: Dict[str, float], parallel: bool = True) -> float:

@@ -61,7 +61,7 @@ def test_confined_chain_is_bitwise_equal(dtype):
         ref = oracle.forward(spec, w, invs[2], row_source=lambda t, r: workload.table_rows(spec, t, r),
                              want_pooled=False)
         got = b[2].out[:400].double().cpu().numpy()
-        assert oracle.check_close(got, ref["out"], ref["out_mag"], RTOL[dtype])["ok"]
+        assert oracle.check_output(got, ref["out"], ref["out_mag"], RTOL[dtype])["ok"]
     finally:
         f.release()
         pool.destroy()

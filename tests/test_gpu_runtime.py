@@ -42,7 +42,7 @@ def _check_inv(spec, weights, dinv, rtol):
     got = to_f64(dinv.out)[:dinv.batch]
     tables = [workload.full_table(spec, t) for t in range(spec.n_tables)]
     res = oracle.forward(spec, weights, dinv.inv, tables=tables, want_pooled=False)
-    c = oracle.check_close(got, res["out"], res["out_mag"], rtol)
+    c = oracle.check_output(got, res["out"], res["out_mag"], rtol)
     assert c["ok"], c
     return c
 

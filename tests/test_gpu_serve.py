@@ -74,7 +74,7 @@ def test_serve_each_result_equals_its_isolated_invocation():
             s = specs[tr.fns[k]]
             ref = oracle.forward(s, workload.weights_arrays(s), tr.invs[k],
                                  row_source=lambda t, r, s=s: workload.table_rows(s, t, r), want_pooled=False)
-            assert oracle.check_close(tr.outs[k], ref["out"], ref["out_mag"], RTOL[s.dtype])["ok"]
+            assert oracle.check_output(tr.outs[k], ref["out"], ref["out_mag"], RTOL[s.dtype])["ok"]
         for f in fns:
             f.release()
     finally:
@@ -118,7 +118,7 @@ def test_serve_admits_by_memory_and_evicts_idle_functions():
             if k % 7 == 0:
                 ref = oracle.forward(s, workload.weights_arrays(s), tr.invs[k],
                                      row_source=lambda t, r, s=s: workload.table_rows(s, t, r), want_pooled=False)
-                assert oracle.check_close(tr.outs[k], ref["out"], ref["out_mag"], RTOL["bf16"])["ok"]
+                assert oracle.check_output(tr.outs[k], ref["out"], ref["out_mag"], RTOL["bf16"])["ok"]
     finally:
         pool.destroy()
 

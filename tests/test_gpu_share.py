@@ -171,7 +171,7 @@ def test_two_processes_map_one_staged_copy(key):
     tables = [workload.full_table(spec, t) for t in range(spec.n_tables)]
     for (B, seed), got in zip(_sizes(), res[0][1]):
         ref = oracle.forward(spec, w, workload.make_invocation(spec, B, seed=seed), tables=tables, want_pooled=False)
-        c = oracle.check_close(got.astype(np.float64), ref["out"], ref["out_mag"], RTOL[spec.dtype])
+        c = oracle.check_output(got.astype(np.float64), ref["out"], ref["out_mag"], RTOL[spec.dtype])
         assert c["ok"], c
 
 
@@ -245,7 +245,7 @@ def test_attach_within_one_process_and_local_sharing():
         got = to_f64(d1.out)[:B]
         ref = oracle.forward(spec, workload.weights_arrays(spec), d1.inv,
                              tables=[workload.full_table(spec, t) for t in range(spec.n_tables)], want_pooled=False)
-        assert oracle.check_close(got, ref["out"], ref["out_mag"], RTOL["f32"])["ok"]
+        assert oracle.check_output(got, ref["out"], ref["out_mag"], RTOL["f32"])["ok"]
         f1.release()
         f2.release()
         assert user.stats()["functions"] == 0

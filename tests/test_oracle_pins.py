@@ -317,3 +317,20 @@ def test_setup_latency_model_reproduces_table_tb_stage():
 def test_throughput_perf_definition():
     # Throughput_theo = T_period / T_comp; perf = app / theo
     assert oracle.throughput_perf(50.0, 10.0, 0.1) == 0.5
+
+
+def test_check_output_applies_the_plain_relative_bound():
+    """Final outputs must meet |got - ref| <= rtol |ref| as well as the magnitude-scaled
+    bound: a 4% error under a loose bound (a deep network's magnitude sum) fails, fp32
+    rounding noise passes, an exact result passes."""
+    ref = np.array([0.5, 0.25, 0.9])
+    mag = np.array([1e4, 1e4, 1e4])
+    wrong = ref * 1.04
+    assert oracle.check_close(wrong, ref, mag, 1e-5)["ok"]
+    c = oracle.check_output(wrong, ref, mag, 1e-5)
+    assert not c["ok"] and c["n_bad_plain"] == 3
+    noisy = ref * (1 + 3e-7)
+    assert oracle.check_output(noisy, ref, mag, 1e-5)["ok"]
+    assert oracle.check_output(ref.copy(), ref, mag, 1e-5)["ok"]
+    # the componentwise bound still applies on its own
+    assert not oracle.check_output(ref + 1e-3, ref, np.full(3, 1.0), 1e-5)["ok"]
