@@ -857,7 +857,10 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   if (ps2 && nb >= 2 && bottom01_fusable(e->layers[0].in, e->layers[0].out, e->layers[1].out)) {
     const Layer& L0 = e->layers[0];
     const Layer& L1 = e->layers[1];
-    const GemmCfg c = tuned_gemm(kBottom01, M, L1.out, L1.in);
+    GemmCfg c = tuned_gemm(kBottom01, M, L1.out, L1.in);
+    // untuned: a persistent CTA spends ~30 us on its tile whatever M is, so below
+    // about 64 tiles the separate kernels, spread over more CTAs, finish first
+    if (c.bn == 0 && (M + 127) / 128 < 64) c = GemmCfg{1, 1};
     if (c.bn != 1) {
       const bool three = nb >= 3 && (c.bn == 0 || c.stages == 202) &&
                          bottom012_fusable(L1.out, e->layers[2].out, M);

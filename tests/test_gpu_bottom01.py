@@ -95,13 +95,24 @@ def test_fused_bottom_equals_separate_kernels_bitwise(pool, case):
 
 
 def test_fused_bottom_is_the_default_and_counts_launches(pool):
-    """Untuned, the batching workload's bottom MLP (13-512-256-64) runs as one kernel: two
-    launches fewer per batch than with separate kernels pinned."""
+    """Untuned, the batching workload's bottom MLP (13-512-256-64) runs as one kernel on a
+    large batch (two launches fewer than with separate kernels pinned) and as separate
+    kernels on a small one."""
     spec = _spec("b01_launches", 13, (512, 256, 64))
-    f = prepare(pool, spec, max_batch=4096)
+    f = prepare(pool, spec, max_batch=12000)
     try:
-        invs = [workload.make_invocation(spec, B, seed=950 + i) for i, B in enumerate([300, 211])]
-        M = 511
+        small = [workload.make_invocation(spec, 300, seed=949)]
+        _run(f, small)
+        n0 = sage.kernel_launches()
+        s_default = _run(f, small)
+        n_small = sage.kernel_launches() - n0
+        sage.tuning_set(KIND_BOTTOM01, 300, 256, 512, *SEPARATE)
+        n0 = sage.kernel_launches()
+        s_sep = _run(f, small)
+        assert sage.kernel_launches() - n0 == n_small   # below 64 tiles: separate kernels by default
+        assert _same(s_default[0], s_sep[0])
+        invs = [workload.make_invocation(spec, B, seed=950 + i) for i, B in enumerate([6000, 3011])]
+        M = 9011
         _run(f, invs)
         n0 = sage.kernel_launches()
         a = _run(f, invs)
