@@ -23,16 +23,18 @@ struct Acc {
 
 __device__ __forceinline__ uint4 ldg_nc_v4(const uint4* p) { return __ldg(p); }
 
-// Two independent fp32 additions (round to nearest) in one instruction: the low
-// halves and the high halves of two 64-bit registers, as two scalar adds would.
-__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b) {
-  uint64_t r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+// acc + the bf16 in the low / high half of w, one fp32 rounding: the mixed-precision
+// add converts the bf16 exactly and adds it to the fp32 accumulator, as unpacking it
+// to fp32 and adding would, without the unpacking instruction.
+__device__ __forceinline__ float add_bf16_lo(uint32_t w, float acc) {
+  float r;
+  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tadd.rn.f32.bf16 %0, l, %2;\n\t}" : "=f"(r) : "r"(w), "f"(acc));
   return r;
 }
-
-__device__ __forceinline__ uint64_t pack2(uint32_t lo, uint32_t hi) {
-  return static_cast<uint64_t>(lo) | (static_cast<uint64_t>(hi) << 32);
+__device__ __forceinline__ float add_bf16_hi(uint32_t w, float acc) {
+  float r;
+  asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %1;\n\tadd.rn.f32.bf16 %0, h, %2;\n\t}" : "=f"(r) : "r"(w), "f"(acc));
+  return r;
 }
 
 template <bool BF16, int LPR, int VPL, int U>
@@ -57,16 +59,12 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
     const char* base = a.tables + a.table_off[t];
     const unsigned rows = static_cast<unsigned>(a.table_rows[t]);
 
-    // running sums: bf16 rows as fp32 pairs added two at a time (element 2e in the low
-    // half, 2e+1 in the high half); fp32 rows one by one (repacking their 16-byte
-    // loads into pairs costs more than it saves).  Either way each element gets the
-    // same sequence of round-to-nearest fp32 additions.
-    uint64_t acc2[VPL][EPV / 2];
+    // running fp32 sums, one per element: bf16 elements added by mixed-precision adds
+    // (element 2e is the low half of word e), fp32 elements by plain adds; either way
+    // each element gets the same sequence of round-to-nearest fp32 additions.
     float acc[VPL][EPV];
 #pragma unroll
     for (int w = 0; w < VPL; ++w) {
-#pragma unroll
-      for (int e = 0; e < EPV / 2; ++e) acc2[w][e] = 0;
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
     }
@@ -96,10 +94,12 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
 #pragma unroll
         for (int w = 0; w < VPL; ++w) {
           if (BF16) {
-            // a bf16 is the top half of its fp32 value
             const uint32_t wd[4] = {v[u][w].x, v[u][w].y, v[u][w].z, v[u][w].w};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc2[w][e] = add_f32x2(acc2[w][e], pack2(wd[e] << 16, wd[e] & 0xffff0000u));
+            for (int e = 0; e < 4; ++e) {
+              acc[w][2 * e] = add_bf16_lo(wd[e], acc[w][2 * e]);
+              acc[w][2 * e + 1] = add_bf16_hi(wd[e], acc[w][2 * e + 1]);
+            }
           } else {
             acc[w][0] += __uint_as_float(v[u][w].x);
             acc[w][1] += __uint_as_float(v[u][w].y);
@@ -118,15 +118,6 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       for (; q + RPW * U <= cnt; q += RPW * U)
         step(q, cnt, my, std::integral_constant<int, U>(), std::false_type());
       for (; q < cnt; q += RPW * UT) step(q, cnt, my, std::integral_constant<int, UT>(), std::true_type());
-    }
-    if (BF16) {
-#pragma unroll
-      for (int w = 0; w < VPL; ++w)
-#pragma unroll
-        for (int e = 0; e < EPV / 2; ++e) {
-          acc[w][2 * e] = __uint_as_float(static_cast<uint32_t>(acc2[w][e]));
-          acc[w][2 * e + 1] = __uint_as_float(static_cast<uint32_t>(acc2[w][e] >> 32));
-        }
     }
     // combine the RPW sub-group partial sums (fixed tree; a+b == b+a exactly)
 #pragma unroll
