@@ -9,6 +9,7 @@
 // order; the RPW partial sums are then combined by a fixed xor tree.  The order
 // of every sum therefore depends only on the bag itself, never on the batch it
 // runs in, which makes fused and isolated invocations bitwise identical.
+#include <algorithm>
 #include <type_traits>
 
 #include "kernels.h"
@@ -37,9 +38,9 @@ __device__ __forceinline__ float add_bf16_hi(uint32_t w, float acc) {
   return r;
 }
 
-template <bool BF16, int LPR, int VPL, int U>
+template <bool BF16, int LPR, int VPL, int U, int RUN>
 __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a,
-                                                     const __grid_constant__ InvTable tab) {
+                                                     const __grid_constant__ InvTable tab, int run) {
   constexpr int RPW = 32 / LPR;
   constexpr int EPV = BF16 ? 8 : 4;  // elements per 16-byte vector
   const int lane = threadIdx.x & 31;
@@ -49,9 +50,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   const size_t row_bytes = static_cast<size_t>(a.dim) * (BF16 ? 2 : 4);
 
-  // bag (t, r): table t, batch row r
-  auto bag_sum = [&](int t, int r) {
-    const int i = tab.n == 1 ? 0 : find_inv(tab, r);
+  // bag (t, r): table t, batch row r of invocation i
+  auto bag_sum = [&](int t, int r, int i) {
     const InvDesc& d = tab.d[i];
     const int64_t bag = static_cast<int64_t>(t) * d.batch + (r - d.row_base);
     const int64_t beg = d.offsets[bag];
@@ -157,40 +157,68 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       }
     }
   };
-  // grid-stride over the T*M bags, table-major; 32-bit index arithmetic whenever the
-  // bag count allows it (a 64-bit division per bag is a long instruction sequence)
+  // grid-stride over runs of `run` (<= RUN) consecutive bags (table-major: consecutive
+  // rows of one table, moving to the next table after row M - 1).  Inside a run the
+  // table, the row and its invocation advance incrementally, so the division and the
+  // invocation search happen once per run; 32-bit index arithmetic whenever the bag
+  // count allows it (a 64-bit division is a long instruction sequence).  RUN = 1
+  // compiles to one bag per step, without the run's extra live registers.
+  auto walk = [&](int t, int r, int cnt) {
+    int i = tab.n == 1 ? 0 : find_inv(tab, r);
+    if constexpr (RUN == 1) {
+      bag_sum(t, r, i);
+    } else {
+      for (int k = 0;;) {
+        bag_sum(t, r, i);
+        if (++k == cnt) break;
+        if (++r == tab.M) {
+          r = 0;
+          ++t;
+          i = 0;
+        }
+        while (i + 1 < tab.n && tab.d[i + 1].row_base <= r) ++i;
+      }
+    }
+  };
   const int64_t first = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  if (G + nwarps < (int64_t(1) << 32)) {
+  const int64_t runs = (G + run - 1) / run;
+  if (G + nwarps * run < (int64_t(1) << 32)) {
     const uint32_t M = static_cast<uint32_t>(tab.M), G32 = static_cast<uint32_t>(G);
-    const uint32_t step = static_cast<uint32_t>(nwarps);
-    for (uint32_t g = static_cast<uint32_t>(first); g < G32; g += step) {
-      const uint32_t t = g / M;
-      bag_sum(static_cast<int>(t), static_cast<int>(g - t * M));
+    const uint32_t step = static_cast<uint32_t>(nwarps), R32 = static_cast<uint32_t>(runs);
+    for (uint32_t q = static_cast<uint32_t>(first); q < R32; q += step) {
+      const uint32_t g0 = q * static_cast<uint32_t>(run);
+      const uint32_t t = g0 / M;
+      walk(static_cast<int>(t), static_cast<int>(g0 - t * M), static_cast<int>(min(static_cast<uint32_t>(run), G32 - g0)));
     }
   } else {
-    for (int64_t g = first; g < G; g += nwarps) {
-      const int t = static_cast<int>(g / tab.M);
-      bag_sum(t, static_cast<int>(g - static_cast<int64_t>(t) * tab.M));
+    for (int64_t q = first; q < runs; q += nwarps) {
+      const int64_t g0 = q * run;
+      const int t = static_cast<int>(g0 / tab.M);
+      walk(t, static_cast<int>(g0 - static_cast<int64_t>(t) * tab.M), static_cast<int>(G - g0 < run ? G - g0 : run));
     }
   }
 }
 
-template <bool BF16, int LPR, int VPL, int U>
+template <bool BF16, int LPR, int VPL, int U, int RUN>
 cudaError_t launch_one(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
   static int blocks_per_sm = -1, sms = 0;
   if (blocks_per_sm < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_kernel<BF16, LPR, VPL, U>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_kernel<BF16, LPR, VPL, U, RUN>, 256, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   const int64_t bags = static_cast<int64_t>(a.T) * tab.M;
   if (bags == 0) return cudaSuccess;
-  int64_t need = (bags + 7) / 8;
+  // runs of up to RUN bags per warp once there are several bags per resident warp;
+  // small batches keep one bag per warp, for parallelism
+  const int64_t resident = static_cast<int64_t>(sms) * blocks_per_sm * 8;
+  const int run = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(RUN, bags / (4 * resident))));
+  int64_t need = ((bags + run - 1) / run + 7) / 8;
   int64_t grid = static_cast<int64_t>(sms) * blocks_per_sm;
   if (need < grid) grid = need;
-  gather_kernel<BF16, LPR, VPL, U><<<static_cast<unsigned>(grid), 256, 0, s>>>(a, tab);
+  gather_kernel<BF16, LPR, VPL, U, RUN><<<static_cast<unsigned>(grid), 256, 0, s>>>(a, tab, run);
   count_launch();
   return cudaGetLastError();
 }
@@ -199,19 +227,19 @@ template <bool BF16>
 cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
   const int rb = a.dim * (BF16 ? 2 : 4);
   switch (rb) {
-    case 16: return launch_one<BF16, 1, 1, 1>(a, tab, s);
-    case 32: return launch_one<BF16, 2, 1, 1>(a, tab, s);
-    case 64: return launch_one<BF16, 4, 1, 2>(a, tab, s);
-    case 128: return launch_one<BF16, 8, 1, 4>(a, tab, s);
+    case 16: return launch_one<BF16, 1, 1, 1, 1>(a, tab, s);
+    case 32: return launch_one<BF16, 2, 1, 1, 1>(a, tab, s);
+    case 64: return launch_one<BF16, 4, 1, 2, 1>(a, tab, s);
+    case 128: return launch_one<BF16, 8, 1, 4, 1>(a, tab, s);
     // 256-byte rows: fp32 as 8 lanes x 32 B (four rows per load instruction, half the
     // index shuffles and address arithmetic per row); bf16 as 16 lanes x 16 B, which
     // keeps its accumulators within 64 registers (measured: fp32 -6% gather time,
     // bf16 +2% with the other shape)
     case 256:
-      if constexpr (BF16) return launch_one<BF16, 16, 1, 8>(a, tab, s);
-      else return launch_one<BF16, 8, 2, 4>(a, tab, s);
-    case 512: return launch_one<BF16, 32, 1, 8>(a, tab, s);
-    case 1024: return launch_one<BF16, 32, 2, 4>(a, tab, s);
+      if constexpr (BF16) return launch_one<BF16, 16, 1, 8, 4>(a, tab, s);
+      else return launch_one<BF16, 8, 2, 4, 1>(a, tab, s);
+    case 512: return launch_one<BF16, 32, 1, 8, 1>(a, tab, s);
+    case 1024: return launch_one<BF16, 32, 2, 4, 1>(a, tab, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -220,20 +248,20 @@ cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
 
 void preload_gather_kernels() {
   cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 1, 1, 1>);
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 2, 1, 1>);
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 4, 1, 2>);
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 1, 4>);
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 2, 4>);
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 1, 8>);
-  cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 2, 4>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 1, 1, 1>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 2, 1, 1>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 4, 1, 2>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 8, 1, 4>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 16, 1, 8>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 1, 8>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 2, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 1, 1, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 2, 1, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 4, 1, 2, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 1, 4, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 2, 4, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 1, 8, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 2, 4, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 1, 1, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 2, 1, 1, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 4, 1, 2, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 8, 1, 4, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 16, 1, 8, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 1, 8, 1>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 2, 4, 1>);
 }
 
 cudaError_t launch_gather(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
