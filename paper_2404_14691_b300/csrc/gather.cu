@@ -230,13 +230,13 @@ cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
     case 16: return launch_one<BF16, 1, 1, 1, 1>(a, tab, s);
     case 32: return launch_one<BF16, 2, 1, 1, 1>(a, tab, s);
     case 64: return launch_one<BF16, 4, 1, 2, 1>(a, tab, s);
-    case 128: return launch_one<BF16, 8, 1, 4, 1>(a, tab, s);
+    case 128: return launch_one<BF16, 8, 1, 4, BF16 ? 4 : 1>(a, tab, s);
     // 256-byte rows: fp32 as 8 lanes x 32 B (four rows per load instruction, half the
     // index shuffles and address arithmetic per row); bf16 as 16 lanes x 16 B, which
     // keeps its accumulators within 64 registers (measured: fp32 -6% gather time,
     // bf16 +2% with the other shape)
     case 256:
-      if constexpr (BF16) return launch_one<BF16, 16, 1, 8, 4>(a, tab, s);
+      if constexpr (BF16) return launch_one<BF16, 16, 1, 8, 8>(a, tab, s);
       else return launch_one<BF16, 8, 2, 4, 1>(a, tab, s);
     case 512: return launch_one<BF16, 32, 1, 8, 1>(a, tab, s);
     case 1024: return launch_one<BF16, 32, 2, 4, 1>(a, tab, s);
@@ -258,8 +258,8 @@ void preload_gather_kernels() {
   cudaFuncGetAttributes(&fa, gather_kernel<true, 1, 1, 1, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<true, 2, 1, 1, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<true, 4, 1, 2, 1>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 8, 1, 4, 1>);
-  cudaFuncGetAttributes(&fa, gather_kernel<true, 16, 1, 8, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 8, 1, 4, 4>);
+  cudaFuncGetAttributes(&fa, gather_kernel<true, 16, 1, 8, 8>);
   cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 1, 8, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<true, 32, 2, 4, 1>);
 }
