@@ -38,6 +38,115 @@ __device__ __forceinline__ float add_bf16_hi(uint32_t w, float acc) {
   return r;
 }
 
+
+// acc += one 16-byte vector of a row (bf16: 8 elements, element 2e the low half of
+// word e; fp32: 4 elements), one round-to-nearest fp32 addition per element.
+template <bool BF16>
+__device__ __forceinline__ void accumulate(float* acc, const uint4& v) {
+  if (BF16) {
+    const uint32_t wd[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      acc[2 * e] = add_bf16_lo(wd[e], acc[2 * e]);
+      acc[2 * e + 1] = add_bf16_hi(wd[e], acc[2 * e + 1]);
+    }
+  } else {
+    acc[0] += __uint_as_float(v.x);
+    acc[1] += __uint_as_float(v.y);
+    acc[2] += __uint_as_float(v.z);
+    acc[3] += __uint_as_float(v.w);
+  }
+}
+
+// Combine the 32 / LPR sub-group partial sums of a bag (fixed xor tree; a + b == b + a
+// exactly) and write the pooled row (bf16, fp32, or fp32 as tf32 hi / residual lo).
+template <bool BF16, int LPR, int VPL>
+__device__ __forceinline__ void finish_bag(float (&acc)[VPL][BF16 ? 8 : 4], const GatherArgs& a, int t, int r,
+                                           int sub, int col) {
+  constexpr int EPV = BF16 ? 8 : 4;
+#pragma unroll
+  for (int o = LPR; o < 32; o <<= 1)
+#pragma unroll
+    for (int w = 0; w < VPL; ++w)
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) acc[w][e] += __shfl_xor_sync(0xffffffffu, acc[w][e], o);
+  if (sub != 0) return;
+  char* orow = static_cast<char*>(a.out) +
+               (static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim) * (BF16 ? 2 : 4);
+#pragma unroll
+  for (int w = 0; w < VPL; ++w) {
+    uint4 o;
+    if (BF16) {
+      o.x = pack_bf16x2(acc[w][0], acc[w][1]);
+      o.y = pack_bf16x2(acc[w][2], acc[w][3]);
+      o.z = pack_bf16x2(acc[w][4], acc[w][5]);
+      o.w = pack_bf16x2(acc[w][6], acc[w][7]);
+    } else if (a.out_lo) {
+      // hi/lo planes for the fp32 tensor-core layers: hi = tf32(sum), lo = sum - hi
+      float h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        h[e] = to_tf32_rna(acc[w][e]);
+        l[e] = acc[w][e] - h[e];
+      }
+      o = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+      float* lrow = a.out_lo + static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim;
+      reinterpret_cast<float4*>(lrow)[col + w * LPR] = make_float4(l[0], l[1], l[2], l[3]);
+    } else {
+      o = make_uint4(__float_as_uint(acc[w][0]), __float_as_uint(acc[w][1]), __float_as_uint(acc[w][2]),
+                     __float_as_uint(acc[w][3]));
+    }
+    reinterpret_cast<uint4*>(orow)[col + w * LPR] = o;
+  }
+}
+
+// Grid-stride over runs of `run` (<= RUN) consecutive bags (table-major: consecutive
+// rows of one table, moving to the next table after row M - 1), calling
+// bag_sum(t, r, i) for table t, batch row r of invocation i.  Inside a run the table,
+// the row and its invocation advance incrementally, so the division and the
+// invocation search happen once per run; 32-bit index arithmetic whenever the bag
+// count allows it (a 64-bit division is a long instruction sequence).  RUN = 1
+// compiles to one bag per step, without the run's extra live registers.
+template <int RUN, class F>
+__device__ __forceinline__ void walk_bags(const InvTable& tab, int T, int run, F&& bag_sum) {
+  const int64_t G = static_cast<int64_t>(T) * tab.M;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  auto walk = [&](int t, int r, int cnt) {
+    int i = tab.n == 1 ? 0 : find_inv(tab, r);
+    if constexpr (RUN == 1) {
+      bag_sum(t, r, i);
+    } else {
+      for (int k = 0;;) {
+        bag_sum(t, r, i);
+        if (++k == cnt) break;
+        if (++r == tab.M) {
+          r = 0;
+          ++t;
+          i = 0;
+        }
+        while (i + 1 < tab.n && tab.d[i + 1].row_base <= r) ++i;
+      }
+    }
+  };
+  const int64_t first = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t runs = (G + run - 1) / run;
+  if (G + nwarps * run < (int64_t(1) << 32)) {
+    const uint32_t M = static_cast<uint32_t>(tab.M), G32 = static_cast<uint32_t>(G);
+    const uint32_t step = static_cast<uint32_t>(nwarps), R32 = static_cast<uint32_t>(runs);
+    for (uint32_t q = static_cast<uint32_t>(first); q < R32; q += step) {
+      const uint32_t g0 = q * static_cast<uint32_t>(run);
+      const uint32_t t = g0 / M;
+      walk(static_cast<int>(t), static_cast<int>(g0 - t * M), static_cast<int>(min(static_cast<uint32_t>(run), G32 - g0)));
+    }
+  } else {
+    for (int64_t q = first; q < runs; q += nwarps) {
+      const int64_t g0 = q * run;
+      const int t = static_cast<int>(g0 / tab.M);
+      walk(t, static_cast<int>(g0 - static_cast<int64_t>(t) * tab.M), static_cast<int>(G - g0 < run ? G - g0 : run));
+    }
+  }
+}
+
 template <bool BF16, int LPR, int VPL, int U, int RUN>
 __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a,
                                                      const __grid_constant__ InvTable tab, int run) {
@@ -46,8 +155,6 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPR;
   const int col = lane % LPR;
-  const int64_t G = static_cast<int64_t>(a.T) * tab.M;
-  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   const size_t row_bytes = static_cast<size_t>(a.dim) * (BF16 ? 2 : 4);
 
   // bag (t, r): table t, batch row r of invocation i
@@ -92,21 +199,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       for (int u = 0; u < UU; ++u) {
         if (!ok[u]) continue;
 #pragma unroll
-        for (int w = 0; w < VPL; ++w) {
-          if (BF16) {
-            const uint32_t wd[4] = {v[u][w].x, v[u][w].y, v[u][w].z, v[u][w].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              acc[w][2 * e] = add_bf16_lo(wd[e], acc[w][2 * e]);
-              acc[w][2 * e + 1] = add_bf16_hi(wd[e], acc[w][2 * e + 1]);
-            }
-          } else {
-            acc[w][0] += __uint_as_float(v[u][w].x);
-            acc[w][1] += __uint_as_float(v[u][w].y);
-            acc[w][2] += __uint_as_float(v[u][w].z);
-            acc[w][3] += __uint_as_float(v[u][w].w);
-          }
-        }
+        for (int w = 0; w < VPL; ++w) accumulate<BF16>(acc[w], v[u][w]);
       }
     };
     constexpr int UT = U < 2 ? U : 2;  // tail: fewer loads per step, fewer idle slots
@@ -119,84 +212,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
         step(q, cnt, my, std::integral_constant<int, U>(), std::false_type());
       for (; q < cnt; q += RPW * UT) step(q, cnt, my, std::integral_constant<int, UT>(), std::true_type());
     }
-    // combine the RPW sub-group partial sums (fixed tree; a+b == b+a exactly)
-#pragma unroll
-    for (int o = LPR; o < 32; o <<= 1)
-#pragma unroll
-      for (int w = 0; w < VPL; ++w)
-#pragma unroll
-        for (int e = 0; e < EPV; ++e) acc[w][e] += __shfl_xor_sync(0xffffffffu, acc[w][e], o);
-
-    if (sub == 0) {
-      char* orow = static_cast<char*>(a.out) +
-                   (static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim) * (BF16 ? 2 : 4);
-#pragma unroll
-      for (int w = 0; w < VPL; ++w) {
-        uint4 o;
-        if (BF16) {
-          o.x = pack_bf16x2(acc[w][0], acc[w][1]);
-          o.y = pack_bf16x2(acc[w][2], acc[w][3]);
-          o.z = pack_bf16x2(acc[w][4], acc[w][5]);
-          o.w = pack_bf16x2(acc[w][6], acc[w][7]);
-        } else if (a.out_lo) {
-          // hi/lo planes for the fp32 tensor-core layers: hi = tf32(sum), lo = sum - hi
-          float h[4], l[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            h[e] = to_tf32_rna(acc[w][e]);
-            l[e] = acc[w][e] - h[e];
-          }
-          o = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
-          float* lrow = a.out_lo + static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim;
-          reinterpret_cast<float4*>(lrow)[col + w * LPR] = make_float4(l[0], l[1], l[2], l[3]);
-        } else {
-          o = make_uint4(__float_as_uint(acc[w][0]), __float_as_uint(acc[w][1]), __float_as_uint(acc[w][2]),
-                         __float_as_uint(acc[w][3]));
-        }
-        reinterpret_cast<uint4*>(orow)[col + w * LPR] = o;
-      }
-    }
+    finish_bag<BF16, LPR, VPL>(acc, a, t, r, sub, col);
   };
-  // grid-stride over runs of `run` (<= RUN) consecutive bags (table-major: consecutive
-  // rows of one table, moving to the next table after row M - 1).  Inside a run the
-  // table, the row and its invocation advance incrementally, so the division and the
-  // invocation search happen once per run; 32-bit index arithmetic whenever the bag
-  // count allows it (a 64-bit division is a long instruction sequence).  RUN = 1
-  // compiles to one bag per step, without the run's extra live registers.
-  auto walk = [&](int t, int r, int cnt) {
-    int i = tab.n == 1 ? 0 : find_inv(tab, r);
-    if constexpr (RUN == 1) {
-      bag_sum(t, r, i);
-    } else {
-      for (int k = 0;;) {
-        bag_sum(t, r, i);
-        if (++k == cnt) break;
-        if (++r == tab.M) {
-          r = 0;
-          ++t;
-          i = 0;
-        }
-        while (i + 1 < tab.n && tab.d[i + 1].row_base <= r) ++i;
-      }
-    }
-  };
-  const int64_t first = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t runs = (G + run - 1) / run;
-  if (G + nwarps * run < (int64_t(1) << 32)) {
-    const uint32_t M = static_cast<uint32_t>(tab.M), G32 = static_cast<uint32_t>(G);
-    const uint32_t step = static_cast<uint32_t>(nwarps), R32 = static_cast<uint32_t>(runs);
-    for (uint32_t q = static_cast<uint32_t>(first); q < R32; q += step) {
-      const uint32_t g0 = q * static_cast<uint32_t>(run);
-      const uint32_t t = g0 / M;
-      walk(static_cast<int>(t), static_cast<int>(g0 - t * M), static_cast<int>(min(static_cast<uint32_t>(run), G32 - g0)));
-    }
-  } else {
-    for (int64_t q = first; q < runs; q += nwarps) {
-      const int64_t g0 = q * run;
-      const int t = static_cast<int>(g0 / tab.M);
-      walk(t, static_cast<int>(g0 - static_cast<int64_t>(t) * tab.M), static_cast<int>(G - g0 < run ? G - g0 : run));
-    }
-  }
+  walk_bags<RUN>(tab, a.T, run, bag_sum);
 }
 
 template <bool BF16, int LPR, int VPL, int U, int RUN>
