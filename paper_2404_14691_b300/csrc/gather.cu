@@ -133,10 +133,27 @@ __device__ __forceinline__ void walk_bags(const InvTable& tab, int T, int run, F
   if (G + nwarps * run < (int64_t(1) << 32)) {
     const uint32_t M = static_cast<uint32_t>(tab.M), G32 = static_cast<uint32_t>(G);
     const uint32_t step = static_cast<uint32_t>(nwarps), R32 = static_cast<uint32_t>(runs);
-    for (uint32_t q = static_cast<uint32_t>(first); q < R32; q += step) {
-      const uint32_t g0 = q * static_cast<uint32_t>(run);
-      const uint32_t t = g0 / M;
-      walk(static_cast<int>(t), static_cast<int>(g0 - t * M), static_cast<int>(min(static_cast<uint32_t>(run), G32 - g0)));
+    if constexpr (RUN == 1) {
+      // one bag per step: the table and row advance by the grid's warp count without a division
+      uint32_t g = static_cast<uint32_t>(first);
+      uint32_t t = g / M, r = g - t * M;
+      const uint32_t dt = step / M, dr = step - dt * M;
+      for (; g < G32; g += step) {
+        walk(static_cast<int>(t), static_cast<int>(r), 1);
+        t += dt;
+        r += dr;
+        if (r >= M) {
+          r -= M;
+          ++t;
+        }
+      }
+    } else {
+      for (uint32_t q = static_cast<uint32_t>(first); q < R32; q += step) {
+        const uint32_t g0 = q * static_cast<uint32_t>(run);
+        const uint32_t t = g0 / M;
+        walk(static_cast<int>(t), static_cast<int>(g0 - t * M),
+             static_cast<int>(min(static_cast<uint32_t>(run), G32 - g0)));
+      }
     }
   } else {
     for (int64_t q = first; q < runs; q += nwarps) {
