@@ -28,20 +28,38 @@ struct InvDesc {
   int64_t nidx;            // indices of the invocation if known on the host (cost model only), else 0
 };
 
+constexpr int kInvBlocks = 1024;
+
 struct InvTable {
   int n;                   // invocations
   int M;                   // total rows
   InvDesc d[kMaxInv];
+  // coarse index for n > 1: blk[k] = the invocation owning row k << blk_shift
+  // (index_invocations fills it on the host)
+  int blk_shift;
+  uint8_t blk[kInvBlocks];
 };
 
-// Index of the invocation owning packed row r (row_base ascending).
-__device__ __forceinline__ int find_inv(const InvTable& tab, int r) {
-  int lo = 0, hi = tab.n - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (tab.d[mid].row_base <= r) lo = mid; else hi = mid - 1;
+// Fill the coarse index of a table whose n, M and row bases are set.
+inline void index_invocations(InvTable& t) {
+  int shift = 0;
+  while (t.M > 0 && ((t.M - 1) >> shift) >= kInvBlocks) ++shift;
+  t.blk_shift = shift;
+  const int nb = t.M > 0 ? ((t.M - 1) >> shift) + 1 : 0;
+  int i = 0;
+  for (int k = 0; k < nb; ++k) {
+    while (i + 1 < t.n && t.d[i + 1].row_base <= (k << shift)) ++i;
+    t.blk[k] = static_cast<uint8_t>(i);
   }
-  return lo;
+}
+
+// Index of the invocation owning packed row r (row_base ascending, n > 1): the
+// coarse index's invocation for r's block, then forward over the invocations that
+// start inside the block.
+__device__ __forceinline__ int find_inv(const InvTable& tab, int r) {
+  int i = tab.blk[r >> tab.blk_shift];
+  while (i + 1 < tab.n && tab.d[i + 1].row_base <= r) ++i;
+  return i;
 }
 
 // ---------------------------------------------------------------- head order

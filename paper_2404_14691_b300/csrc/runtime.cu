@@ -1498,6 +1498,7 @@ sage_status sage_invoke_batch(sage_fn f, const sage_invocation* invs, int n, voi
     }
     tab->M = static_cast<int>(M);
     if (tab->n == 0) continue;
+    index_invocations(*tab);
     st = run_batch(e, *tab, s);
     if (st != SAGE_OK) return st;
     e->pool->invocations += tab->n;
@@ -1648,6 +1649,7 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
       row += v.batch;
     }
     tab->M = static_cast<int>(row);
+    index_invocations(*tab);
     for (auto& r : dense_r) add(r.dst, r.src, r.n);
     for (auto& r : idx_r) add(r.dst, r.src, r.n);
     for (auto& r : off_r) add(r.dst, r.src, r.n);
