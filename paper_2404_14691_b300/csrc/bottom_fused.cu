@@ -1,4 +1,5 @@
-// Bottom layers 0 and 1 of an fp32 function in one persistent kernel.
+// Bottom layers 0 and 1 (and optionally 2) of an fp32 function in one persistent
+// kernel.
 //
 // Layer 0 (K0 <= 15 dense inputs -> N0 outputs, ReLU) has too little arithmetic for
 // the tensor cores and would otherwise write N0 activations per row (as two tf32
