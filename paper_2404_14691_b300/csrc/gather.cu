@@ -258,6 +258,139 @@ cudaError_t launch_one(const GatherArgs& a, const InvTable& tab, cudaStream_t s)
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- bag per lane group
+//
+// For short bags the per-bag work (invocation, offsets, table base, the sub-group
+// combine, the output) outweighs the row loads.  Here a warp's 32 / LPR lane groups
+// each own a bag: the per-bag work runs once for all of them, in the same
+// instructions, and no combine is needed.  A group reads its bag's rows one at a
+// time (LPR lanes x VPL x 16 bytes = one row), U rows in flight, and each lane adds
+// its pieces in bag order: one fixed order per bag, whatever the batch.  The warp
+// loops to the longest of its bags; the other groups' lanes idle meanwhile.
+template <bool BF16, int LPR, int VPL, int U>
+__global__ void __launch_bounds__(256) gather_group_kernel(const __grid_constant__ GatherArgs a,
+                                                           const __grid_constant__ InvTable tab) {
+  constexpr int NG = 32 / LPR;
+  constexpr int EPV = BF16 ? 8 : 4;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / LPR;
+  const int gl = lane % LPR;
+  const uint32_t M = static_cast<uint32_t>(tab.M), T = static_cast<uint32_t>(a.T);
+  const uint32_t slots = ((gridDim.x * blockDim.x) >> 5) * NG;  // bags per grid step
+  const uint32_t first = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * NG + grp;
+  const size_t row_bytes = static_cast<size_t>(a.dim) * (BF16 ? 2 : 4);
+  // table and row of this group's bag, advanced by `slots` bags per step without a division
+  uint32_t t = first / M, r = first - t * M;
+  const uint32_t dt = slots / M, dr = slots - dt * M;
+  while (__any_sync(0xffffffffu, t < T)) {
+    int64_t beg = 0, end = 0;
+    const char* base = a.tables;
+    const int32_t* idx = nullptr;
+    unsigned rows = 0;
+    if (t < T) {
+      const int i = tab.n == 1 ? 0 : find_inv(tab, static_cast<int>(r));
+      const InvDesc& d = tab.d[i];
+      const int64_t bag = static_cast<int64_t>(t) * d.batch + (static_cast<int>(r) - d.row_base);
+      beg = d.offsets[bag];
+      end = d.offsets[bag + 1];
+      base = a.tables + a.table_off[t] + gl * (VPL * 16);
+      rows = static_cast<unsigned>(a.table_rows[t]);
+      idx = d.indices + beg;
+    }
+    const int len = static_cast<int>(end - beg);
+    int maxlen = len;
+#pragma unroll
+    for (int o = LPR; o < 32; o <<= 1) maxlen = max(maxlen, __shfl_xor_sync(0xffffffffu, maxlen, o));
+    float acc[VPL][EPV];
+#pragma unroll
+    for (int w = 0; w < VPL; ++w)
+#pragma unroll
+      for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
+    for (int j0 = 0; j0 < maxlen; j0 += LPR) {
+      const int my = j0 + gl < len ? __ldg(idx + j0 + gl) : 0;  // the group's next LPR indices
+      const int cnt = min(LPR, maxlen - j0);
+      for (int p = 0; p < cnt; p += U) {
+        uint4 v[U][VPL];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int q = p + u;
+          const int row = __shfl_sync(0xffffffffu, my, grp * LPR + (q & (LPR - 1)));
+          ok[u] = q < cnt && j0 + q < len;
+          if (ok[u] && static_cast<unsigned>(row) >= rows) {
+            ok[u] = false;
+            if (a.err) atomicOr(a.err, kErrBounds);
+          }
+          const uint4* src = reinterpret_cast<const uint4*>(base + static_cast<size_t>(ok[u] ? row : 0) * row_bytes);
+#pragma unroll
+          for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (!ok[u]) continue;
+#pragma unroll
+          for (int w = 0; w < VPL; ++w) accumulate<BF16>(acc[w], v[u][w]);
+        }
+      }
+    }
+    if (t < T) {
+      // the group's pooled row: lane gl holds elements [gl * VPL * EPV, ...)
+      const size_t o = static_cast<size_t>(r) * a.ldo + static_cast<size_t>(t) * a.dim;
+#pragma unroll
+      for (int w = 0; w < VPL; ++w) {
+        uint4 ov;
+        if (BF16) {
+          ov.x = pack_bf16x2(acc[w][0], acc[w][1]);
+          ov.y = pack_bf16x2(acc[w][2], acc[w][3]);
+          ov.z = pack_bf16x2(acc[w][4], acc[w][5]);
+          ov.w = pack_bf16x2(acc[w][6], acc[w][7]);
+          reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + o)[gl * VPL + w] = ov;
+        } else if (a.out_lo) {
+          float h[4], l[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            h[e] = to_tf32_rna(acc[w][e]);
+            l[e] = acc[w][e] - h[e];
+          }
+          reinterpret_cast<float4*>(static_cast<float*>(a.out) + o)[gl * VPL + w] = make_float4(h[0], h[1], h[2], h[3]);
+          reinterpret_cast<float4*>(a.out_lo + o)[gl * VPL + w] = make_float4(l[0], l[1], l[2], l[3]);
+        } else {
+          reinterpret_cast<float4*>(static_cast<float*>(a.out) + o)[gl * VPL + w] =
+              make_float4(acc[w][0], acc[w][1], acc[w][2], acc[w][3]);
+        }
+      }
+    }
+    t += dt;
+    r += dr;
+    if (r >= M) {
+      r -= M;
+      ++t;
+    }
+  }
+}
+
+template <bool BF16, int LPR, int VPL, int U>
+cudaError_t launch_group(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
+  static int blocks_per_sm = -1, sms = 0;
+  if (blocks_per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_group_kernel<BF16, LPR, VPL, U>, 256, 0);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  constexpr int NG = 32 / LPR;
+  const int64_t bags = static_cast<int64_t>(a.T) * tab.M;
+  if (bags == 0) return cudaSuccess;
+  int64_t need = (bags + 8 * NG - 1) / (8 * NG);
+  int64_t grid = static_cast<int64_t>(sms) * blocks_per_sm;
+  if (need < grid) grid = need;
+  if (bags + grid * 8 * NG >= (int64_t(1) << 32)) return cudaErrorInvalidValue;  // 32-bit bag arithmetic
+  gather_group_kernel<BF16, LPR, VPL, U><<<static_cast<unsigned>(grid), 256, 0, s>>>(a, tab);
+  count_launch();
+  return cudaGetLastError();
+}
+
 template <bool BF16>
 cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
   const int rb = a.dim * (BF16 ? 2 : 4);
@@ -272,6 +405,7 @@ cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
     // bf16 +2% with the other shape)
     case 256:
       if constexpr (BF16) return launch_one<BF16, 16, 1, 8, 8>(a, tab, s);
+      else if (static_cast<int64_t>(a.T) * tab.M < (int64_t(1) << 31)) return launch_group<BF16, 8, 2, 4>(a, tab, s);
       else return launch_one<BF16, 8, 2, 4, 1>(a, tab, s);
     case 512: return launch_one<BF16, 32, 1, 8, 1>(a, tab, s);
     case 1024: return launch_one<BF16, 32, 2, 4, 1>(a, tab, s);
@@ -288,6 +422,7 @@ void preload_gather_kernels() {
   cudaFuncGetAttributes(&fa, gather_kernel<false, 4, 1, 2, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 1, 4, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<false, 8, 2, 4, 1>);
+  cudaFuncGetAttributes(&fa, gather_group_kernel<false, 8, 2, 4>);
   cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 1, 8, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<false, 32, 2, 4, 1>);
   cudaFuncGetAttributes(&fa, gather_kernel<true, 1, 1, 1, 1>);
