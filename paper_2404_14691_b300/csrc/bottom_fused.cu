@@ -159,8 +159,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int k = 0; k < kBK / 8; ++k) {
             const uint32_t o = k * 32;
-            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
-            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+            tc_mma_tf32_fill_a(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc,
+                               (kb | k) != 0 ? 1u : 0u);
+            tc_mma_tf32_lastuse_a(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
             tc_mma_tf32(acc, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
           }
           tc_commit(&empty[s]);
@@ -371,9 +372,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int k = 0; k < kBK / 8; ++k) {
                 const uint32_t o = k * 32;
-                tc_mma_tf32(acc2, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc2,
-                            (kb | k) != 0 ? 1u : 0u);
-                tc_mma_tf32(acc2, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc2, 1u);
+                tc_mma_tf32_fill_a(acc2, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc2,
+                                   (kb | k) != 0 ? 1u : 0u);
+                tc_mma_tf32_lastuse_a(acc2, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc2, 1u);
                 tc_mma_tf32(acc2, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc2, 1u);
               }
             }

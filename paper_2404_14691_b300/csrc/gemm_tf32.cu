@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
         for (int k = 0; k < kBK / 8; ++k) {
           const uint32_t o = k * 32;  // 8 fp32 = 32 bytes along K inside the swizzle row
-          tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
-          tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+          tc_mma_tf32_fill_a(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc,
+                             (kb | k) != 0 ? 1u : 0u);
+          tc_mma_tf32_lastuse_a(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
           tc_mma_tf32(tmem, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
         }
         tc_commit(&empty[s]);
@@ -258,8 +259,9 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
       for (int k = 0; k < kBK / 8; ++k) {
         const uint32_t o = k * 32;
-        tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
-        tc_mma_tf32(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+        tc_mma_tf32_fill_a(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc,
+                           (kb | k) != 0 ? 1u : 0u);
+        tc_mma_tf32_lastuse_a(tmem, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
         tc_mma_tf32(tmem, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
       }
       tc_commit(&empty[s]);
@@ -408,8 +410,9 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
 #pragma unroll
           for (int k = 0; k < kBK / 8; ++k) {
             const uint32_t o = k * 32;
-            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc, (kb | k) != 0 ? 1u : 0u);
-            tc_mma_tf32(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
+            tc_mma_tf32_fill_a(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bh + o), idesc,
+                               (kb | k) != 0 ? 1u : 0u);
+            tc_mma_tf32_lastuse_a(acc, sw128_kmajor_desc(ah + o), sw128_kmajor_desc(bl + o), idesc, 1u);
             tc_mma_tf32(acc, sw128_kmajor_desc(al + o), sw128_kmajor_desc(bh + o), idesc, 1u);
           }
           tc_commit(&empty[s]);
