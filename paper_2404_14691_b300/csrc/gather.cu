@@ -399,10 +399,10 @@ cudaError_t dispatch(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
     case 32: return launch_one<BF16, 2, 1, 1, 1>(a, tab, s);
     case 64: return launch_one<BF16, 4, 1, 2, 1>(a, tab, s);
     case 128: return launch_one<BF16, 8, 1, 4, BF16 ? 4 : 1>(a, tab, s);
-    // 256-byte rows: fp32 as 8 lanes x 32 B (four rows per load instruction, half the
-    // index shuffles and address arithmetic per row); bf16 as 16 lanes x 16 B, which
-    // keeps its accumulators within 64 registers (measured: fp32 -6% gather time,
-    // bf16 +2% with the other shape)
+    // 256-byte rows: fp32 as 8 lanes x 32 B per row, one bag per 8-lane group (short
+    // bags: the per-bag work dominates; one bag per warp only for batches beyond 2^31
+    // bags); bf16 as 16 lanes x 16 B, one bag per warp walking runs of up to 8 bags,
+    // which keeps it within 64 registers (long bags: the rows dominate)
     case 256:
       if constexpr (BF16) return launch_one<BF16, 16, 1, 8, 8>(a, tab, s);
       else if (static_cast<int64_t>(a.T) * tab.M < (int64_t(1) << 31)) return launch_group<BF16, 8, 2, 4>(a, tab, s);
