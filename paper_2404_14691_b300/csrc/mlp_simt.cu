@@ -206,11 +206,11 @@ __global__ void __launch_bounds__(256) bottom0_kernel(const __grid_constant__ In
   }
 }
 
-// Bottom layer 0 for thin inputs (K <= 16): a block owns 32 rows and all N
-// outputs; each thread keeps one output column's weights in registers and walks
-// the block's rows, whose dense features sit in shared memory (broadcast reads).
-// Stores are coalesced along the output row.  Same per-output order as above
-// (k = 0..K-1 FMA chain, then the bias).
+// Bottom layer 0 for thin inputs (K <= 16): a block walks groups of 32 rows
+// (grid-stride) and computes all N outputs of each; each thread keeps one or two
+// output columns' weights in registers for the whole walk, and the group's dense
+// features sit in shared memory (broadcast reads).  Stores are coalesced along the
+// output row.  Same per-output order as above (k = 0..K-1 FMA chain, then the bias).
 template <bool BF16>
 __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant__ InvTable tab, int K, int N,
                                                            const void* __restrict__ Wv,
@@ -219,23 +219,24 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
   constexpr int R = 32, KM = 16;
   __shared__ __align__(16) float sx[R][KM];  // dense rows, zero-padded to KM
   __shared__ const float* srow[R];
-  const int r0 = blockIdx.x * R;
-  if (threadIdx.x < R) {
-    const int r = r0 + threadIdx.x;
-    const float* p = nullptr;
-    if (r < tab.M) {
-      const int i = tab.n == 1 ? 0 : find_inv(tab, r);
-      p = tab.d[i].dense + static_cast<size_t>(r - tab.d[i].row_base) * K;
+  // the group's dense rows into shared memory (callers sync before reuse)
+  auto stage = [&](int r0) {
+    if (threadIdx.x < R) {
+      const int r = r0 + threadIdx.x;
+      const float* p = nullptr;
+      if (r < tab.M) {
+        const int i = tab.n == 1 ? 0 : find_inv(tab, r);
+        p = tab.d[i].dense + static_cast<size_t>(r - tab.d[i].row_base) * K;
+      }
+      srow[threadIdx.x] = p;
     }
-    srow[threadIdx.x] = p;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < R * KM; e += blockDim.x) {
-    const int rr = e / KM, k = e % KM;
-    sx[rr][k] = (srow[rr] && k < K) ? srow[rr][k] : 0.f;
-  }
-  __syncthreads();
-  const int nrows = min(R, tab.M - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < R * KM; e += blockDim.x) {
+      const int rr = e / KM, k = e % KM;
+      sx[rr][k] = (srow[rr] && k < K) ? srow[rr][k] : 0.f;
+    }
+    __syncthreads();
+  };
   auto load_w = [&](int j, float (&w)[KM]) {
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
@@ -263,55 +264,82 @@ __global__ void __launch_bounds__(256) bottom0_thin_kernel(const __grid_constant
     }
     return fmaxf(s + b, 0.f);
   };
+  auto store1 = [&](size_t o, float v) {
+    if (BF16) {
+      reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(v);
+    } else if (y_lo) {
+      const float h = to_tf32_rna(v);
+      reinterpret_cast<float*>(y)[o] = h;
+      y_lo[o] = v - h;
+    } else {
+      reinterpret_cast<float*>(y)[o] = v;
+    }
+  };
   // two adjacent columns per thread (one 8-byte / bf16-pair store per row and plane)
-  // when the layout allows it, else one
+  // when the layout allows it
   const bool pairs = (N % 2 == 0) && (ldy % 2 == 0) && !(reinterpret_cast<uintptr_t>(y) & 7) &&
                      !(reinterpret_cast<uintptr_t>(y_lo) & 7);
-  if (pairs) {
-    for (int j = 2 * static_cast<int>(threadIdx.x); j < N; j += 2 * blockDim.x) {
-      float w0[KM], w1[KM];
+  const int per = pairs ? 2 : 1;
+  if (N <= per * static_cast<int>(blockDim.x)) {
+    // every column of the layer has its thread: weights stay in registers for the walk
+    const int j = per * static_cast<int>(threadIdx.x);
+    const bool act = j < N;
+    float w0[KM], w1[KM];
+    float b0 = 0.f, b1 = 0.f;
+    if (act) {
       load_w(j, w0);
-      load_w(j + 1, w1);
-      const float b0 = bias[j], b1 = bias[j + 1];
-      for (int rr = 0; rr < nrows; ++rr) {
-        float4 x[KM / 4];
+      b0 = bias[j];
+      if (pairs) {
+        load_w(j + 1, w1);
+        b1 = bias[j + 1];
+      }
+    }
+    for (int r0 = blockIdx.x * R; r0 < tab.M; r0 += gridDim.x * R) {
+      stage(r0);
+      const int nrows = min(R, tab.M - r0);
+      if (act) {
+        for (int rr = 0; rr < nrows; ++rr) {
+          float4 x[KM / 4];
 #pragma unroll
-        for (int q = 0; q < KM / 4; ++q) x[q] = reinterpret_cast<const float4*>(&sx[rr][0])[q];  // broadcasts
-        const float s0 = dot(x, w0, b0), s1 = dot(x, w1, b1);
-        const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
-        if (BF16) {
-          *reinterpret_cast<uint32_t*>(reinterpret_cast<__nv_bfloat16*>(y) + o) = pack_bf16x2(s0, s1);
-        } else if (y_lo) {
-          const float h0 = to_tf32_rna(s0), h1 = to_tf32_rna(s1);
-          *reinterpret_cast<float2*>(reinterpret_cast<float*>(y) + o) = make_float2(h0, h1);
-          *reinterpret_cast<float2*>(y_lo + o) = make_float2(s0 - h0, s1 - h1);
-        } else {
-          *reinterpret_cast<float2*>(reinterpret_cast<float*>(y) + o) = make_float2(s0, s1);
+          for (int q = 0; q < KM / 4; ++q) x[q] = reinterpret_cast<const float4*>(&sx[rr][0])[q];  // broadcasts
+          const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
+          const float s0 = dot(x, w0, b0);
+          if (pairs) {
+            const float s1 = dot(x, w1, b1);
+            if (BF16) {
+              *reinterpret_cast<uint32_t*>(reinterpret_cast<__nv_bfloat16*>(y) + o) = pack_bf16x2(s0, s1);
+            } else if (y_lo) {
+              const float h0 = to_tf32_rna(s0), h1 = to_tf32_rna(s1);
+              *reinterpret_cast<float2*>(reinterpret_cast<float*>(y) + o) = make_float2(h0, h1);
+              *reinterpret_cast<float2*>(y_lo + o) = make_float2(s0 - h0, s1 - h1);
+            } else {
+              *reinterpret_cast<float2*>(reinterpret_cast<float*>(y) + o) = make_float2(s0, s1);
+            }
+          } else {
+            store1(o, s0);
+          }
         }
       }
+      __syncthreads();  // before the next group overwrites sx
     }
     return;
   }
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    float w[KM];
-    load_w(j, w);
-    const float bj = bias[j];
-    for (int rr = 0; rr < nrows; ++rr) {
-      float4 x[KM / 4];
+  // wider layers: columns in strides of the block, weights reloaded per group
+  for (int r0 = blockIdx.x * R; r0 < tab.M; r0 += gridDim.x * R) {
+    stage(r0);
+    const int nrows = min(R, tab.M - r0);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+      float w[KM];
+      load_w(j, w);
+      const float bj = bias[j];
+      for (int rr = 0; rr < nrows; ++rr) {
+        float4 x[KM / 4];
 #pragma unroll
-      for (int q = 0; q < KM / 4; ++q) x[q] = reinterpret_cast<const float4*>(&sx[rr][0])[q];
-      const float s = dot(x, w, bj);
-      const size_t o = static_cast<size_t>(r0 + rr) * ldy + j;
-      if (BF16) {
-        reinterpret_cast<__nv_bfloat16*>(y)[o] = __float2bfloat16_rn(s);
-      } else if (y_lo) {
-        const float h = to_tf32_rna(s);
-        reinterpret_cast<float*>(y)[o] = h;
-        y_lo[o] = s - h;
-      } else {
-        reinterpret_cast<float*>(y)[o] = s;
+        for (int q = 0; q < KM / 4; ++q) x[q] = reinterpret_cast<const float4*>(&sx[rr][0])[q];
+        store1(static_cast<size_t>(r0 + rr) * ldy + j, dot(x, w, bj));
       }
     }
+    __syncthreads();
   }
 }
 
@@ -404,7 +432,8 @@ cudaError_t launch_bottom0(int dtype, const InvTable& tab, int K, int N, const v
   if (tab.M <= 0) return cudaSuccess;
   if (K < 1 || K > 64) return cudaErrorInvalidValue;
   if (K <= 16) {
-    const int blocks = (tab.M + 31) / 32;
+    // groups of 32 rows, walked by one wave of blocks (4 per SM at <= 64 registers)
+    const int blocks = std::min((tab.M + 31) / 32, sms() * 4);
     if (dtype == 1) bottom0_thin_kernel<true><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy, nullptr);
     else bottom0_thin_kernel<false><<<blocks, 256, 0, s>>>(tab, K, N, W, bias, y, ldy, y_lo);
     count_launch();
