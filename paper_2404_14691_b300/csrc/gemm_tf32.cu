@@ -316,13 +316,18 @@ __global__ void __launch_bounds__(128, 1)
 //   warp 0 lane 0: TMA producer; warp 1 lane 0: MMA issuer;
 //   warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
 // With HEAD the epilogue writes no Y: it fuses the sigmoid head (HeadParams).
+// Without HEAD, when the last wave of tiles would leave more than half of the CTAs
+// idle, its tiles run as two half-width items each (B maps tmBh2 / tmBl2, boxes of
+// BN / 2 rows), so that wave takes half as long; the MMAs per output element are the
+// same, so are the bits.
 template <int BN, int NST, bool HEAD>
 __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, const CUtensorMap& tmAl,
                                                        const CUtensorMap& tmBh, const CUtensorMap& tmBl, int M,
                                                        int N, int K, const float* __restrict__ bias, int relu,
                                                        float* __restrict__ Yh, float* __restrict__ Yl, int ldy,
                                                        int* err, const HeadParams* hp, const CUtensorMap* tmYh,
-                                                       const CUtensorMap* tmYl) {
+                                                       const CUtensorMap* tmYl, const CUtensorMap* tmBh2 = nullptr,
+                                                       const CUtensorMap* tmBl2 = nullptr) {
   using C = Tf32Cfg<BN, NST>;
   static_assert(HEAD || C::STAGES * C::STAGE >= 4 * 32768, "last-tile output staging: 32 KB per epilogue warp");
   extern __shared__ uint8_t smem_raw[];
@@ -341,6 +346,25 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
   const int KB = (K + kBK - 1) / kBK;
   const int NT = N / BN, MT = (M + kBM - 1) / kBM;
   const int tiles = NT * MT;
+  // work items: tiles, the last wave's split in halves when that halves its time
+  const int GR = static_cast<int>(gridDim.x);
+  int nfull = tiles, items = tiles;
+  if (!HEAD && tmBh2 && tiles > GR && tiles % GR != 0 && 2 * (tiles % GR) <= GR) {
+    nfull = tiles - tiles % GR;
+    items = nfull + 2 * (tiles % GR);
+  }
+  auto item = [&](int w, int& m0, int& n0, int& width) {
+    if (w < nfull) {
+      m0 = (w / NT) * kBM;
+      n0 = (w % NT) * BN;
+      width = BN;
+    } else {
+      const int h = w - nfull, t = nfull + h / 2;
+      m0 = (t / NT) * kBM;
+      n0 = (t % NT) * BN + (h & 1) * (BN / 2);
+      width = BN / 2;
+    }
+  };
 
   if (warp == 0) tmem_alloc(tmem_slot, 2 * BN);
   if (warp == 1 && lane == 0) {
@@ -369,8 +393,10 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
     if (lane == 0) {
       uint32_t g = 0;  // stage use counter across tiles
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
+        int m0, n0, width;
+        item(w, m0, n0, width);
+        const bool whole = width == BN;
         for (int kb = 0; kb < KB; ++kb, ++g) {
           const int s = g % C::STAGES;
           const uint32_t ph = (g / C::STAGES) & 1;
@@ -378,21 +404,22 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[s], C::STAGE);
+          mbar_arrive_expect_tx(&full[s], whole ? C::STAGE : C::STAGE - C::B_BYTES);
           tma_load_2d(a_hi(s), &tmAh, kb * kBK, m0, &full[s]);
           tma_load_2d(a_lo(s), &tmAl, kb * kBK, m0, &full[s]);
-          tma_load_2d(b_hi(s), &tmBh, kb * kBK, n0, &full[s]);
-          tma_load_2d(b_lo(s), &tmBl, kb * kBK, n0, &full[s]);
+          tma_load_2d(b_hi(s), whole ? &tmBh : tmBh2, kb * kBK, n0, &full[s]);
+          tma_load_2d(b_lo(s), whole ? &tmBl : tmBl2, kb * kBK, n0, &full[s]);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32_f32(kBM, BN);
+      constexpr uint32_t idesc_whole = idesc_tf32_f32(kBM, BN), idesc_half = idesc_tf32_f32(kBM, BN / 2);
       uint32_t g = 0;
       int i = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x, ++i) {
+        const uint32_t idesc = w < nfull ? idesc_whole : idesc_half;
         const int buf = i & 1;
         const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
         if (!mbar_wait(&acc_empty[buf], ((i >> 1) & 1) ^ 1, err)) break;
@@ -424,9 +451,10 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
     // ---- epilogue warps
     const int q = warp & 3;
     int i = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+    for (int w = blockIdx.x; w < items; w += gridDim.x, ++i) {
       const int buf = i & 1;
-      const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      int m0, n0, width;
+      item(w, m0, n0, width);
       if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
       tc_fence_after();
       const int row = m0 + q * 32 + lane;
@@ -462,18 +490,18 @@ __device__ __forceinline__ void tf32x3_persistent_body(const CUtensorMap& tmAh, 
         if (row < M) head_row<BN / 64>(*hp, row, gs, static_cast<unsigned>(n0 / 64), G);
         continue;
       }
-      if (t + static_cast<int>(gridDim.x) >= tiles) {
+      if (w + static_cast<int>(gridDim.x) >= items) {
         // the CTA's last tile: out through the idle stage ring and TMA stores
         tail_store_f32_planes<BN, 4>(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16),
                                   smem + q * 32768, lane, bias, relu != 0, tmYh, tmYl, n0, m0 + q * 32,
-                                  m0 + q * 32 < M);
+                                  m0 + q * 32 < M, 0, 1, width);
         tc_fence_before();
         mbar_arrive(&acc_empty[buf]);
         continue;
       }
       const size_t ro = static_cast<size_t>(row < M ? row : 0) * ldy + n0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < width; c0 += 32) {
         uint32_t v[32];
         tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
         tmem_ld_wait();
@@ -518,10 +546,11 @@ __global__ void __launch_bounds__(192, 1)
     gemm_tf32x3_persistent_kernel(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
                                   const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl,
                                   const __grid_constant__ CUtensorMap tmYh, const __grid_constant__ CUtensorMap tmYl,
+                                  const __grid_constant__ CUtensorMap tmBh2, const __grid_constant__ CUtensorMap tmBl2,
                                   int M, int N, int K, const float* __restrict__ bias, int relu,
                                   float* __restrict__ Yh, float* __restrict__ Yl, int ldy, int* err) {
   tf32x3_persistent_body<BN, NST, false>(tmAh, tmAl, tmBh, tmBl, M, N, K, bias, relu, Yh, Yl, ldy, err, nullptr,
-                                         &tmYh, &tmYl);
+                                         &tmYh, &tmYl, &tmBh2, &tmBl2);
 }
 
 template <int BN, int NST>
@@ -587,15 +616,16 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const float* xh, const flo
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms_p, cudaDevAttrMultiProcessorCount, dev);
   }
-  CUtensorMap tah, tal, tbh, tbl, tyh, tyl;
+  CUtensorMap tah, tal, tbh, tbl, tyh, tyl, tbh2, tbl2;
   if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
       !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN) ||
+      !make_tmap_2d(&tbh2, 0, wh, N, K, K, kBK, BN / 2) || !make_tmap_2d(&tbl2, 0, wl, N, K, K, kBK, BN / 2) ||
       !make_tmap_2d(&tyh, 0, yh, M, N, ldy, 32, 32) || !make_tmap_2d(&tyl, 0, yl, M, N, ldy, 32, 32))
     return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
   const int grid = tiles < g_sms_p ? tiles : g_sms_p;
   gemm_tf32x3_persistent_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(
-      tah, tal, tbh, tbl, tyh, tyl, M, N, K, bias, relu, yh, yl, ldy, err);
+      tah, tal, tbh, tbl, tyh, tyl, tbh2, tbl2, M, N, K, bias, relu, yh, yl, ldy, err);
   count_launch();
   return cudaGetLastError();
 }

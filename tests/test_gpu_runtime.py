@@ -585,3 +585,34 @@ def test_bounded_wait_times_out_then_completes(pool):
         assert f.query() == sage.SAGE_OK
     finally:
         f.release()
+
+
+@pytest.mark.parametrize("tile", [(128, 103), (64, 104)])
+def test_fp32_persistent_last_wave_split_bitwise(pool, tile):
+    """A persistent fp32 layer whose last wave of tiles is short runs that wave as
+    half-width items; the outputs keep the bits of the non-persistent kernel."""
+    torch = _torch()
+    spec = workload.spec_tiny(key="rt_split_%d" % tile[0], dtype="f32", n_tables=4, rows=5000, dim=64,
+                              bot=(128, 64), top=(256, 128, 1), l_min=0, l_max=20)
+    f = prepare(pool, spec, max_batch=4000)
+    try:
+        invs = [workload.make_invocation(spec, B, seed=1200 + i) for i, B in enumerate([3500, 3500, 3500])]
+        M = 10500                                       # 83 row tiles: 166 or 332 column tiles
+        for (K, N) in [(320, 256), (256, 128)]:
+            sage.tuning_set(3, M, N, K, 64, 4)          # non-persistent reference
+        ref = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in ref])
+        torch.cuda.synchronize()
+        sage.tuning_set(3, M, 256, 320, tile[0], tile[1])
+        got = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in got])
+        torch.cuda.synchronize()
+        f.check_errors()
+        for a, b in zip(ref, got):
+            assert torch.equal(a.out, b.out)
+        rows = np.arange(0, 3500, 251)
+        ref_o, mag = oracle_rows(spec, workload.weights_arrays(spec), invs[2], rows)
+        c = oracle.check_output(to_f64(got[2].out)[rows], ref_o, mag, RTOL["f32"])
+        assert c["ok"], c
+    finally:
+        f.release()
