@@ -43,6 +43,22 @@ std::string gpu_name() {
   return s;
 }
 
+// Median of five timed runs (CUDA events on the stream; the run was warmed up once).
+template <class Run>
+float median_of_5(Run& run, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  float t[5];
+  for (int r = 0; r < 5; ++r) {
+    cudaEventRecord(e0, s);
+    run();
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    t[r] = 0;
+    cudaEventElapsedTime(&t[r], e0, e1);
+  }
+  std::sort(t, t + 5);
+  return t[2];
+}
+
 }  // namespace
 
 GemmCfg tuned_gemm(int kind, int M, int N, int K) {
@@ -101,19 +117,9 @@ sage_status autotune_gemm(int kind, int M, int N, int K, cudaStream_t s, GemmCfg
       cudaGetLastError();
       continue;
     }
-    std::vector<float> t;
-    for (int r = 0; r < 5; ++r) {
-      cudaEventRecord(e0, s);
-      run();
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      t.push_back(ms);
-    }
-    std::sort(t.begin(), t.end());
-    if (t[2] < best_t) {
-      best_t = t[2];
+    const float t = median_of_5(run, s, e0, e1);
+    if (t < best_t) {
+      best_t = t;
       best = cands[c];
     }
   }
@@ -208,19 +214,9 @@ sage_status autotune_bottom01(int M, int K0, int N0, int N1, int N2, cudaStream_
       cudaGetLastError();
       continue;
     }
-    std::vector<float> t;
-    for (int r = 0; r < 5; ++r) {
-      cudaEventRecord(e0, s);
-      run();
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      t.push_back(ms);
-    }
-    std::sort(t.begin(), t.end());
-    if (t[2] < best_t) {
-      best_t = t[2];
+    const float t = median_of_5(run, s, e0, e1);
+    if (t < best_t) {
+      best_t = t;
       best = cands[c];
     }
   }
