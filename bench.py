@@ -189,6 +189,41 @@ def oracle_rate(spec, invs, budget_s: float, threads: int):
     return done / el, done, samples, el
 
 
+def roofline_of(kind: str, nl: int, tms: float, work: float, peaks: dict, peak_src: str) -> dict:
+    """Achieved rate of one kernel kind (algorithmic work per launch / mean launch time)
+    against its bound: HBM copy rate for the gather, tensor peaks for the GEMMs."""
+    avg_s = tms / nl / 1e3
+    per_launch = work / nl
+    if kind == "gather":
+        peak = peaks["hbm_gbs"]
+        achieved = per_launch / avg_s / 1e9
+        return {"kernel": kind, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src + " (hbm_gbs copy)"}
+    if kind == "gemm_tc":
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        achieved = per_launch / avg_s / 1e12
+        return {"kernel": kind, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_src + " (bf16_tflops_sustained)"}
+    if kind in ("gemm_tf32x3", "bottom01"):
+        # fp32 on the tensor cores as three tf32 products: the ceiling for useful fp32
+        # flops is the tf32 peak / 3; tf32 peak = measured bf16 x nominal tf32/bf16 (1.1/2.25).
+        # (bottom01's flops include its layer 0, ~5% of them, which runs on the FP32 pipes)
+        tf32 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.1 / 2.25)
+        peak = tf32 / 3.0
+        achieved = per_launch / avg_s / 1e12
+        return {"kernel": kind, "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "peak_source": peak_src + " bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (three tf32 "
+                               "products per fp32 product)"}
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    achieved = per_launch / avg_s / 1e12
+    return {"kernel": kind, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
+            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+            "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz}
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, rank, world, local_rank):
@@ -390,46 +425,18 @@ def run_ours(args, rank, world, local_rank):
     e2e_match = bool(torch.equal(dev_out, h_out))
     clocks = sampler.stop()
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel (and of every kernel kind, for the metric's
+    # "gather HBM GB/s" and "MLP TC util")
     peaks, peak_src = load_peaks()
+    rooflines = {kind: roofline_of(kind, nl, tms, work, peaks, peak_src) for kind, (nl, tms, work) in prof.items()}
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
     if dom:
         kind, (nl, tms, work) = dom
-        avg_s = tms / nl / 1e3
-        per_launch = work / nl
-        if kind == "gather":
-            peak = peaks["hbm_gbs"]
-            achieved = per_launch / avg_s / 1e9
-            roof = {"kernel": kind, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                    "frac": round(achieved / peak, 4), "peak_source": peak_src + " (hbm_gbs copy)"}
-        elif kind == "gemm_tc":
-            peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-            achieved = per_launch / avg_s / 1e12
-            roof = {"kernel": kind, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "peak_source": peak_src + " (bf16_tflops_sustained)"}
-        elif kind == "gemm_tf32x3":
-            # fp32 on the tensor cores as three tf32 products: the ceiling for useful fp32
-            # flops is the tf32 peak / 3; tf32 peak = measured bf16 x nominal tf32/bf16 (1.1/2.25)
-            tf32 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.1 / 2.25)
-            peak = tf32 / 3.0
-            achieved = per_launch / avg_s / 1e12
-            roof = {"kernel": kind, "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "peak_source": peak_src + " bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (three tf32 "
-                                   "products per fp32 product)"}
-        else:
-            mhz = peaks.get("sm_max_mhz", 2032.0)
-            peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
-            achieved = per_launch / avg_s / 1e12
-            roof = {"kernel": kind, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
-                    "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz}
-        tr = traffic_for(kind, args.workload)
-        roof["traffic"] = tr
+        roof = dict(rooflines[kind])
+        roof["traffic"] = traffic_for(kind, args.workload)
         roof["launches_per_step"] = nl / len(prof_times)
-        roof["work_per_launch"] = per_launch
+        roof["work_per_launch"] = work / nl
     kernels = {k: {"launches": v[0], "ms_per_step": round(v[1] / len(prof_times), 4),
                    "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)} for k, v in prof.items()}
 
@@ -455,6 +462,8 @@ def run_ours(args, rank, world, local_rank):
                     "K": int(t[3]), "bn": int(t[4]), "stages": int(t[5])} for t in tuning],
         "kernels": kernels,
         "roofline": roof,
+        "rooflines_by_kernel": {k: {x: v[x] for x in ("bound", "achieved", "peak", "unit", "frac")}
+                                for k, v in rooflines.items()},
         "e2e": {"value": round(world * n_inv * e2e_steps / e2e_s, 2), "unit": "invocations/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "matches_device_path": e2e_match,
                 "ms_per_step": round(e2e_s / e2e_steps * 1e3, 4),
