@@ -36,3 +36,24 @@ def test_committed_traffic_entries_name_existing_sources():
         for kind, rec in kernels.items():
             assert os.path.exists(os.path.join(bench.ROOT, "paper_2404_14691_b300", "csrc", rec["source"])), (wl, kind)
             assert rec["dram_bytes_per_launch"] > 0 and len(rec["source_sha256_16"]) == 16
+
+
+def test_roofline_of_each_kernel_kind():
+    """achieved = work per launch / mean launch time, against the kind's bound."""
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1500.0, "sm_max_mhz": 2000.0}
+    # 4 launches in 2 ms in all, 8e9 bytes of work in all: 2e9 B per 0.5 ms = 4000 GB/s
+    g = bench.roofline_of("gather", 4, 2.0, 8e9, peaks, "test")
+    assert g["bound"] == "hbm" and g["unit"] == "GB/s" and abs(g["achieved"] - 4000.0) < 1e-6
+    assert abs(g["frac"] - 4000.0 / 6000.0) < 1e-4
+    # bf16 GEMMs against the sustained bf16 peak: 3e12 flop in 2 ms over 2 launches = 1500 TF/s
+    t = bench.roofline_of("gemm_tc", 2, 2.0, 3e12, peaks, "test")
+    assert t["bound"] == "tensor" and abs(t["achieved"] - 1500.0) < 1e-6 and abs(t["frac"] - 1.0) < 1e-4
+    # fp32 as three tf32 products (and the fused bottom kernel): tf32 = bf16 x 1.1 / 2.25, / 3
+    ceiling = 1500.0 * 1.1 / 2.25 / 3.0
+    for kind in ("gemm_tf32x3", "bottom01"):
+        f = bench.roofline_of(kind, 1, 1.0, 1e11, peaks, "test")   # 100 TF/s
+        assert f["bound"] == "tensor" and abs(f["peak"] - round(ceiling, 1)) < 1e-6
+        assert abs(f["frac"] - 100.0 / ceiling) < 1e-3
+    # anything else: the FP32 pipes at the maximum SM clock
+    a = bench.roofline_of("bottom0", 1, 1.0, 1e10, peaks, "test")
+    assert a["bound"] == "alu" and abs(a["peak"] - 148 * 128 * 2 * 2000e6 / 1e12) < 0.01
