@@ -139,11 +139,13 @@ __global__ void __launch_bounds__(128, 1)
 // MMA; warps 2-5: epilogue (warp w reads TMEM lanes 32*(w%4)..+31).
 // With HEAD the epilogue writes no Y: it fuses the sigmoid head (HeadParams) on
 // the bf16-rounded activations, the values the separate head kernel would read.
+// Without HEAD, a last wave of at most half as many tiles as CTAs runs as half-width
+// items (B map tmB2 with boxes of BN / 2 rows), as in the fp32 persistent kernel.
 template <int BN, int NST, bool HEAD>
 __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const CUtensorMap& tmB, int M, int N,
                                                    int K, const float* __restrict__ bias, int relu,
                                                    __nv_bfloat16* __restrict__ Y, int ldy, int* err,
-                                                   const HeadParams* hp) {
+                                                   const HeadParams* hp, const CUtensorMap* tmB2 = nullptr) {
   using C = TcCfg<BN, NST>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -159,6 +161,24 @@ __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const
   const int KB = (K + kBK - 1) / kBK;
   const int NT = N / BN, MT = (M + kBM - 1) / kBM;
   const int tiles = NT * MT;
+  const int GR = static_cast<int>(gridDim.x);
+  int nfull = tiles, items = tiles;
+  if (!HEAD && tmB2 && tiles > GR && tiles % GR != 0 && 2 * (tiles % GR) <= GR) {
+    nfull = tiles - tiles % GR;
+    items = nfull + 2 * (tiles % GR);
+  }
+  auto item = [&](int w, int& m0, int& n0, int& width) {
+    if (w < nfull) {
+      m0 = (w / NT) * kBM;
+      n0 = (w % NT) * BN;
+      width = BN;
+    } else {
+      const int h = w - nfull, t = nfull + h / 2;
+      m0 = (t / NT) * kBM;
+      n0 = (t % NT) * BN + (h & 1) * (BN / 2);
+      width = BN / 2;
+    }
+  };
 
   if (warp == 0) tmem_alloc(tmem_slot, 2 * BN);
   if (warp == 1 && lane == 0) {
@@ -185,8 +205,10 @@ __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const
     if (lane == 0) {
       uint32_t g = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x) {
+        int m0, n0, width;
+        item(w, m0, n0, width);
+        const bool whole = width == BN;
         for (int kb = 0; kb < KB; ++kb, ++g) {
           const int s = g % C::STAGES;
           const uint32_t ph = (g / C::STAGES) & 1;
@@ -194,19 +216,20 @@ __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&full[s], C::STAGE);
+          mbar_arrive_expect_tx(&full[s], whole ? C::STAGE : C::STAGE - C::B_BYTES / 2);
           tma_load_2d(sA + s * C::A_BYTES, &tmA, kb * kBK, m0, &full[s]);
-          tma_load_2d(sB + s * C::B_BYTES, &tmB, kb * kBK, n0, &full[s]);
+          tma_load_2d(sB + s * C::B_BYTES, whole ? &tmB : tmB2, kb * kBK, n0, &full[s]);
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(kBM, BN);
+      constexpr uint32_t idesc_whole = idesc_bf16_f32(kBM, BN), idesc_half = idesc_bf16_f32(kBM, BN / 2);
       uint32_t g = 0;
       int i = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++i) {
+      for (int w = blockIdx.x; w < items && ok; w += gridDim.x, ++i) {
+        const uint32_t idesc = w < nfull ? idesc_whole : idesc_half;
         const int buf = i & 1;
         const uint32_t acc = tmem + static_cast<uint32_t>(buf * BN);
         if (!mbar_wait(&acc_empty[buf], ((i >> 1) & 1) ^ 1, err)) break;
@@ -233,9 +256,10 @@ __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const
   } else {
     const int q = warp & 3;
     int i = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+    for (int w = blockIdx.x; w < items; w += gridDim.x, ++i) {
       const int buf = i & 1;
-      const int m0 = (t / NT) * kBM, n0 = (t % NT) * BN;
+      int m0, n0, width;
+      item(w, m0, n0, width);
       if (!mbar_wait(&acc_full[buf], (i >> 1) & 1, err)) break;
       tc_fence_after();
       const int row = m0 + q * 32 + lane;
@@ -273,7 +297,7 @@ __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const
       }
       __nv_bfloat16* yrow = Y + static_cast<size_t>(row < M ? row : 0) * ldy + n0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < width; c0 += 32) {
         uint32_t v[32];
         tmem_ld_32cols(tmem + static_cast<uint32_t>(buf * BN) + (static_cast<uint32_t>(q * 32) << 16) + c0, v);
         tmem_ld_wait();
@@ -307,9 +331,10 @@ __device__ __forceinline__ void tc_persistent_body(const CUtensorMap& tmA, const
 template <int BN, int NST>
 __global__ void __launch_bounds__(192, 1)
     gemm_tc_persistent_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                              int M, int N, int K, const float* __restrict__ bias, int relu,
-                              __nv_bfloat16* __restrict__ Y, int ldy, int* err) {
-  tc_persistent_body<BN, NST, false>(tmA, tmB, M, N, K, bias, relu, Y, ldy, err, nullptr);
+                              const __grid_constant__ CUtensorMap tmB2, int M, int N, int K,
+                              const float* __restrict__ bias, int relu, __nv_bfloat16* __restrict__ Y, int ldy,
+                              int* err) {
+  tc_persistent_body<BN, NST, false>(tmA, tmB, M, N, K, bias, relu, Y, ldy, err, nullptr, &tmB2);
 }
 
 template <int BN, int NST>
@@ -362,12 +387,13 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const void* x, int ldx, co
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms_pt, cudaDevAttrMultiProcessorCount, dev);
   }
-  CUtensorMap ta, tb;
-  if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
+  CUtensorMap ta, tb, tb2;
+  if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN) || !make_map(&tb2, W, N, K, K, BN / 2))
+    return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
   const int grid = tiles < g_sms_pt ? tiles : g_sms_pt;
   gemm_tc_persistent_kernel<BN, NST><<<grid, 192, TcCfg<BN, NST>::SMEM, s>>>(
-      ta, tb, M, N, K, bias, relu, static_cast<__nv_bfloat16*>(y), ldy, err);
+      ta, tb, tb2, M, N, K, bias, relu, static_cast<__nv_bfloat16*>(y), ldy, err);
   count_launch();
   return cudaGetLastError();
 }

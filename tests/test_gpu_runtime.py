@@ -616,3 +616,34 @@ def test_fp32_persistent_last_wave_split_bitwise(pool, tile):
         assert c["ok"], c
     finally:
         f.release()
+
+
+@pytest.mark.parametrize("tile", [(256, 104), (128, 106)])
+def test_bf16_persistent_last_wave_split_bitwise(pool, tile):
+    """The persistent bf16 layer runs a short last wave as half-width items too; the
+    outputs keep the bits of the non-persistent kernel."""
+    torch = _torch()
+    spec = workload.spec_tiny(key="rt_split16_%d" % tile[0], dtype="bf16", n_tables=4, rows=5000, dim=64,
+                              bot=(128, 64), top=(256, 128, 1), l_min=0, l_max=20)
+    f = prepare(pool, spec, max_batch=7000)
+    try:
+        invs = [workload.make_invocation(spec, 7000, seed=1300 + i) for i in range(3)]
+        M = 21000                                       # 165 row tiles: 165 or 330 column tiles
+        for (K, N) in [(320, 256), (256, 128)]:
+            sage.tuning_set(1, M, N, K, 128, 6)         # non-persistent reference
+        ref = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in ref])
+        torch.cuda.synchronize()
+        sage.tuning_set(1, M, 256, 320, tile[0], tile[1])
+        got = [DevInvocation(v) for v in invs]
+        f.invoke_batch([d.args() for d in got])
+        torch.cuda.synchronize()
+        f.check_errors()
+        for a, b in zip(ref, got):
+            assert torch.equal(a.out, b.out)
+        rows = np.arange(0, 7000, 499)
+        ref_o, mag = oracle_rows(spec, workload.weights_arrays(spec), invs[1], rows)
+        c = oracle.check_output(to_f64(got[1].out)[rows], ref_o, mag, RTOL["bf16"])
+        assert c["ok"], c
+    finally:
+        f.release()
