@@ -166,6 +166,60 @@ __device__ __forceinline__ void walk_bags(const InvTable& tab, int T, int run, F
   }
 }
 
+// One step of a bag: UU row loads in flight per lane, bag positions q + u*RPW + sub of
+// the current 32-index chunk (row indices in lane p of `my`); the position check is
+// needed only in a bag's last, partial steps.  Rows out of the table's range set the
+// bounds error bit and are skipped.
+template <bool BF16, int LPR, int VPL, int UU, bool CHECKED>
+__device__ __forceinline__ void bag_step(float (&acc)[VPL][BF16 ? 8 : 4], const GatherArgs& a, const char* base,
+                                         unsigned rows, int sub, int col, int q, int cnt, int my) {
+  constexpr int RPW = 32 / LPR;
+  constexpr unsigned kRowBytes = LPR * VPL * 16;  // a row is LPR lanes x VPL x 16 bytes
+  const char* lane_base = base + col * 16;
+  uint4 v[UU][VPL];
+  unsigned row[UU];
+#pragma unroll
+  for (int u = 0; u < UU; ++u) row[u] = static_cast<unsigned>(__shfl_sync(0xffffffffu, my, (q + u * RPW + sub) & 31));
+  if constexpr (!CHECKED) {
+    // all UU positions lie in the bag: one range check for the step, the rare
+    // out-of-range step takes the checked path below
+    unsigned hi = row[0];
+#pragma unroll
+    for (int u = 1; u < UU; ++u) hi = max(hi, row[u]);
+    if (hi < rows) {
+#pragma unroll
+      for (int u = 0; u < UU; ++u) {
+        const uint4* src = reinterpret_cast<const uint4*>(lane_base + static_cast<uint64_t>(row[u]) * kRowBytes);
+#pragma unroll
+        for (int w = 0; w < VPL; ++w) v[u][w] = ldg_nc_v4(src + w * LPR);
+      }
+#pragma unroll
+      for (int u = 0; u < UU; ++u)
+#pragma unroll
+        for (int w = 0; w < VPL; ++w) accumulate<BF16>(acc[w], v[u][w]);
+      return;
+    }
+  }
+  bool ok[UU];
+#pragma unroll
+  for (int u = 0; u < UU; ++u) {
+    ok[u] = CHECKED ? q + u * RPW + sub < cnt : true;
+    if (ok[u] && row[u] >= rows) {
+      ok[u] = false;
+      if (a.err) atomicOr(a.err, kErrBounds);
+    }
+    const uint4* src = reinterpret_cast<const uint4*>(lane_base + static_cast<uint64_t>(ok[u] ? row[u] : 0u) * kRowBytes);
+#pragma unroll
+    for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w * LPR) : make_uint4(0, 0, 0, 0);
+  }
+#pragma unroll
+  for (int u = 0; u < UU; ++u) {
+    if (!ok[u]) continue;
+#pragma unroll
+    for (int w = 0; w < VPL; ++w) accumulate<BF16>(acc[w], v[u][w]);
+  }
+}
+
 template <bool BF16, int LPR, int VPL, int U, int RUN>
 __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ GatherArgs a,
                                                      const __grid_constant__ InvTable tab, int run) {
@@ -174,7 +228,6 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
   const int lane = threadIdx.x & 31;
   const int sub = lane / LPR;
   const int col = lane % LPR;
-  const size_t row_bytes = static_cast<size_t>(a.dim) * (BF16 ? 2 : 4);
 
   // bag (t, r): table t, batch row r of invocation i
   auto bag_sum = [&](int t, int r, int i) {
@@ -195,32 +248,6 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
     }
 
-    // one step: UU row loads in flight per lane, positions q + u*RPW + sub; the
-    // position check is needed only in a bag's last, partial steps
-    auto step = [&](int q, int cnt, int my, auto uu, auto checked) {
-      constexpr int UU = decltype(uu)::value;
-      uint4 v[UU][VPL];
-      bool ok[UU];
-#pragma unroll
-      for (int u = 0; u < UU; ++u) {
-        const int p = q + u * RPW + sub;
-        const int row = __shfl_sync(0xffffffffu, my, p & 31);
-        ok[u] = decltype(checked)::value ? p < cnt : true;
-        if (ok[u] && static_cast<unsigned>(row) >= rows) {
-          ok[u] = false;
-          if (a.err) atomicOr(a.err, kErrBounds);
-        }
-        const uint4* src = reinterpret_cast<const uint4*>(base + static_cast<size_t>(ok[u] ? row : 0) * row_bytes) + col;
-#pragma unroll
-        for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w * LPR) : make_uint4(0, 0, 0, 0);
-      }
-#pragma unroll
-      for (int u = 0; u < UU; ++u) {
-        if (!ok[u]) continue;
-#pragma unroll
-        for (int w = 0; w < VPL; ++w) accumulate<BF16>(acc[w], v[u][w]);
-      }
-    };
     constexpr int UT = U < 2 ? U : 2;  // tail: fewer loads per step, fewer idle slots
     for (int64_t j0 = beg; j0 < end; j0 += 32) {
       const int cnt = static_cast<int>(min(static_cast<int64_t>(32), end - j0));
@@ -228,8 +255,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       int q = 0;
       // each lane still adds its positions in increasing order: same sums as one loop
       for (; q + RPW * U <= cnt; q += RPW * U)
-        step(q, cnt, my, std::integral_constant<int, U>(), std::false_type());
-      for (; q < cnt; q += RPW * UT) step(q, cnt, my, std::integral_constant<int, UT>(), std::true_type());
+        bag_step<BF16, LPR, VPL, U, false>(acc, a, base, rows, sub, col, q, cnt, my);
+      for (; q < cnt; q += RPW * UT) bag_step<BF16, LPR, VPL, UT, true>(acc, a, base, rows, sub, col, q, cnt, my);
     }
     finish_bag<BF16, LPR, VPL>(acc, a, t, r, sub, col);
   };
