@@ -248,7 +248,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
       for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
     }
 
-    constexpr int UT = U < 2 ? U : 2;  // tail: fewer loads per step, fewer idle slots
+    // tail steps: fewer loads per step, fewer idle slots; 4 for bf16 256-byte rows (2 or 8
+    // were slower there), 2 elsewhere
+    constexpr int UT = BF16 && LPR == 16 ? 4 : (U < 2 ? U : 2);
     for (int64_t j0 = beg; j0 < end; j0 += 32) {
       const int cnt = static_cast<int>(min(static_cast<int64_t>(32), end - j0));
       const int my = lane < cnt ? __ldg(d.indices + j0 + lane) : 0;
