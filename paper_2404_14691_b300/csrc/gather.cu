@@ -337,16 +337,26 @@ __global__ void __launch_bounds__(256) gather_group_kernel(const __grid_constant
     for (int w = 0; w < VPL; ++w)
 #pragma unroll
       for (int e = 0; e < EPV; ++e) acc[w][e] = 0.f;
-    for (int j0 = 0; j0 < maxlen; j0 += LPR) {
-      const int my = j0 + gl < len ? __ldg(idx + j0 + gl) : 0;  // the group's next LPR indices
-      const int cnt = min(LPR, maxlen - j0);
+    // the group's next CH * LPR indices, CH loads per lane issued together: index
+    // position j0 + m * LPR + gl sits in lane gl's register m
+    constexpr int CH = 32 / LPR;
+    static_assert(U <= LPR && LPR % U == 0, "a step stays within one index register");
+    for (int j0 = 0; j0 < maxlen; j0 += CH * LPR) {
+      int my[CH];
+#pragma unroll
+      for (int m = 0; m < CH; ++m) my[m] = j0 + m * LPR + gl < len ? __ldg(idx + j0 + m * LPR + gl) : 0;
+      const int cnt = min(CH * LPR, maxlen - j0);
       for (int p = 0; p < cnt; p += U) {
         uint4 v[U][VPL];
         bool ok[U];
+        const int mp = p / LPR;  // the register holding positions p .. p + U - 1
+        int src = my[0];
+#pragma unroll
+        for (int m = 1; m < CH; ++m) src = mp == m ? my[m] : src;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           const int q = p + u;
-          const int row = __shfl_sync(0xffffffffu, my, grp * LPR + (q & (LPR - 1)));
+          const int row = __shfl_sync(0xffffffffu, src, grp * LPR + (q & (LPR - 1)));
           ok[u] = q < cnt && j0 + q < len;
           if (ok[u] && static_cast<unsigned>(row) >= rows) {
             ok[u] = false;
