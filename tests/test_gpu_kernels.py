@@ -112,6 +112,42 @@ def test_gather_out_of_range_row_sets_error_and_is_skipped():
     assert oracle.check_close(got, ref, mag, RTOL["f32"])["ok"]
 
 
+@pytest.mark.parametrize("dtype,dim", [("f32", 64), ("bf16", 128), ("bf16", 64), ("f32", 16)])
+def test_gather_out_of_range_rows_in_full_and_tail_steps(dtype, dim):
+    """Long bags (20..60 rows): bad rows inside a full step (the step's single range
+    check fails and the step takes the per-row checked path), in a bag's tail, and in
+    the fp32 lane-group kernel (256-byte rows): error bit set, only the bad rows skipped."""
+    torch = _torch()
+    spec = workload.spec_tiny(key="g_oob2_%s_%d" % (dtype, dim), dtype=dtype, n_tables=3, rows=400, dim=dim,
+                              l_min=20, l_max=60)
+    B = 23
+    inv = workload.make_invocation(spec, B, seed=81)
+    off = inv["offsets"]
+    bad = dict(inv)
+    bad["indices"] = inv["indices"].copy()
+    pos = [int(off[0]) + 3, int(off[1]) - 1, int(off[B + 4]) + 17, int(off[2 * B + 7]) + 1]
+    bad["indices"][pos[0]] = 400          # == rows
+    bad["indices"][pos[1]] = 1 << 30
+    bad["indices"][pos[2]] = -1
+    bad["indices"][pos[3]] = 401
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    got = to_f64(_run_gather(spec, bad, err=err))
+    assert int(err.item()) & 1
+    keep = np.ones(inv["indices"].size, bool)
+    keep[pos] = False
+    off2 = np.array([np.sum(keep[:o]) for o in off], dtype=np.int64)
+    tables = [workload.full_table(spec, t) for t in range(3)]
+    ref, mag = oracle.bag_sum(tables, inv["indices"][keep], off2, B)
+    c = oracle.check_close(got, ref, mag, RTOL[dtype])
+    assert c["ok"], c
+    # without bad rows: no error bit, and the bags that held them now include those rows
+    err.zero_()
+    good = to_f64(_run_gather(spec, inv, err=err))
+    assert int(err.item()) == 0
+    ref, mag = oracle.bag_sum(tables, inv["indices"], off, B)
+    assert oracle.check_close(good, ref, mag, RTOL[dtype])["ok"]
+
+
 # ------------------------------------------------------------------ dense layers
 
 F32_SHAPES = [(1, 64, 16), (127, 512, 576), (300, 256, 512), (1000, 64, 256), (129, 12, 20), (513, 516, 260),
