@@ -24,6 +24,26 @@ struct Acc {
 
 __device__ __forceinline__ uint4 ldg_nc_v4(const uint4* p) { return __ldg(p); }
 
+// The warp's next unit of work from the launch's `next` counter (called by all lanes).
+__device__ __forceinline__ uint32_t claim(unsigned* work) {
+  uint32_t q = 0;
+  if ((threadIdx.x & 31) == 0) q = atomicAdd(work, 1u);
+  return __shfl_sync(0xffffffffu, q, 0);
+}
+
+// End of a block that claimed work: the grid's last block to get here -- every other
+// block has made its final claim by then -- resets both counters for the next launch.
+__device__ __forceinline__ void block_done(unsigned* work) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(work + 1, 1u) == gridDim.x - 1) {
+      atomicExch(work, 0u);
+      atomicExch(work + 1, 0u);
+    }
+  }
+}
+
 // acc + the bf16 in the low / high half of w, one fp32 rounding: the mixed-precision
 // add converts the bf16 exactly and adds it to the fp32 accumulator, as unpacking it
 // to fp32 and adding would, without the unpacking instruction.
@@ -110,7 +130,7 @@ __device__ __forceinline__ void finish_bag(float (&acc)[VPL][BF16 ? 8 : 4], cons
 // count allows it (a 64-bit division is a long instruction sequence).  RUN = 1
 // compiles to one bag per step, without the run's extra live registers.
 template <int RUN, class F>
-__device__ __forceinline__ void walk_bags(const InvTable& tab, int T, int run, F&& bag_sum) {
+__device__ __forceinline__ void walk_bags(const InvTable& tab, int T, int run, unsigned* work, F&& bag_sum) {
   const int64_t G = static_cast<int64_t>(T) * tab.M;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
   auto walk = [&](int t, int r, int cnt) {
@@ -135,7 +155,17 @@ __device__ __forceinline__ void walk_bags(const InvTable& tab, int T, int run, F
   if (G + nwarps * run < (int64_t(1) << 32)) {
     const uint32_t M = static_cast<uint32_t>(tab.M), G32 = static_cast<uint32_t>(G);
     const uint32_t step = static_cast<uint32_t>(nwarps), R32 = static_cast<uint32_t>(runs);
-    if constexpr (RUN == 1) {
+    if (work) {
+      // claimed runs (one bag each for RUN = 1)
+      for (;;) {
+        const uint32_t q = claim(work);
+        if (q >= R32) break;
+        const uint32_t g0 = q * static_cast<uint32_t>(run);
+        const uint32_t t = g0 / M;
+        walk(static_cast<int>(t), static_cast<int>(g0 - t * M),
+             static_cast<int>(min(static_cast<uint32_t>(run), G32 - g0)));
+      }
+    } else if constexpr (RUN == 1) {
       // one bag per step: the table and row advance by the grid's warp count without a division
       uint32_t g = static_cast<uint32_t>(first);
       uint32_t t = g / M, r = g - t * M;
@@ -262,7 +292,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
     }
     finish_bag<BF16, LPR, VPL>(acc, a, t, r, sub, col);
   };
-  walk_bags<RUN>(tab, a.T, run, bag_sum);
+  walk_bags<RUN>(tab, a.T, run, a.work, bag_sum);
+  if (a.work) block_done(a.work);
 }
 
 template <bool BF16, int LPR, int VPL, int U, int RUN>
@@ -310,8 +341,17 @@ __global__ void __launch_bounds__(256) gather_group_kernel(const __grid_constant
   const uint32_t slots = ((gridDim.x * blockDim.x) >> 5) * NG;  // bags per grid step
   const uint32_t first = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * NG + grp;
   const size_t row_bytes = static_cast<size_t>(a.dim) * (BF16 ? 2 : 4);
-  // table and row of this group's bag, advanced by `slots` bags per step without a division
-  uint32_t t = first / M, r = first - t * M;
+  // table and row of this group's bag: claimed NG bags at a time, or advanced by `slots`
+  // bags per step without a division
+  uint32_t t, r;
+  if (a.work) {
+    const uint32_t g = claim(a.work) * NG + grp;
+    t = g / M;
+    r = g - t * M;
+  } else {
+    t = first / M;
+    r = first - t * M;
+  }
   const uint32_t dt = slots / M, dr = slots - dt * M;
   while (__any_sync(0xffffffffu, t < T)) {
     int64_t beg = 0, end = 0;
@@ -401,13 +441,20 @@ __global__ void __launch_bounds__(256) gather_group_kernel(const __grid_constant
         }
       }
     }
-    t += dt;
-    r += dr;
-    if (r >= M) {
-      r -= M;
-      ++t;
+    if (a.work) {
+      const uint32_t g = claim(a.work) * NG + grp;
+      t = g / M;
+      r = g - t * M;
+    } else {
+      t += dt;
+      r += dr;
+      if (r >= M) {
+        r -= M;
+        ++t;
+      }
     }
   }
+  if (a.work) block_done(a.work);
 }
 
 template <bool BF16, int LPR, int VPL, int U>

@@ -35,6 +35,11 @@ struct GatherArgs {
   int ldo;
   int* err;
   float* out_lo = nullptr;           // fp32 only, optional: out becomes the tf32 hi plane, out_lo the residual
+  // optional: two counters {next, done}, zero before the launch and zero again after it
+  // (the last block to finish resets them); with them, warps claim their bags (or runs
+  // of bags) one group at a time instead of a fixed grid-stride share, so blocks that
+  // start early -- beside another kernel that holds part of the GPU -- take more work
+  unsigned* work = nullptr;
 };
 cudaError_t launch_gather(const GatherArgs& a, const InvTable& tab, cudaStream_t s);
 

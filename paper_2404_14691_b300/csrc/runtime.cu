@@ -188,6 +188,7 @@ struct Slot {
   // head fused into the last hidden layer: per-row group sums and arrival counters
   float* hpart = nullptr;
   unsigned* hcnt = nullptr;
+  unsigned* gwork = nullptr;  // the gather's claimed-work counters {next, done}
   char* io = nullptr;
   size_t io_bytes = 0;
   cudaEvent_t done = nullptr;
@@ -584,6 +585,7 @@ size_t slot_bytes(const Entry* e, int cap) {
   for (size_t l = 0; l + 1 < e->top.size(); ++l)
     b += align256(pl * static_cast<size_t>(cap) * e->top[l] * e->elem());
   if (const int G = head_groups(e)) b += align256(static_cast<size_t>(cap) * G * 4) + align256(static_cast<size_t>(cap) * 4);
+  b += align256(2 * sizeof(unsigned));
   return b;
 }
 
@@ -619,6 +621,9 @@ sage_status build_slot(Entry* e, Slot& s, int cap, cudaStream_t stream) {
     o += align256(static_cast<size_t>(cap) * 4);
     SAGE_CK(cudaMemsetAsync(s.hcnt, 0, static_cast<size_t>(cap) * 4, stream));
   }
+  s.gwork = reinterpret_cast<unsigned*>(buf + o);
+  o += align256(2 * sizeof(unsigned));
+  SAGE_CK(cudaMemsetAsync(s.gwork, 0, 2 * sizeof(unsigned), stream));
   return SAGE_OK;
 }
 
@@ -920,6 +925,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     a.ldo = cd;
     a.err = e->d_err;
     a.out_lo = lo_of(s.concat, cd);
+    a.work = s.gwork;
     // algorithmic bytes: each lookup reads a row and its index, each bag reads its
     // offset and writes one pooled row
     double lookups = 0;
@@ -1752,8 +1758,10 @@ sage_status sage_fn_check(sage_fn f) {
   if (w & kErrTimeout) {
     // a kernel that gave up may have left fused-head arrival counters short
     std::lock_guard<std::mutex> g(e->imu);
-    for (auto& s : e->slots)
+    for (auto& s : e->slots) {
       if (s.hcnt) SAGE_CK(cudaMemset(s.hcnt, 0, static_cast<size_t>(s.cap) * 4));
+      if (s.gwork) SAGE_CK(cudaMemset(s.gwork, 0, 2 * sizeof(unsigned)));
+    }
   }
   if (w & kErrTimeout) return fail(SAGE_ERR_DEVICE, "a kernel's bounded wait ran out");
   if (w & kErrBounds) return fail(SAGE_ERR_BOUNDS, "a bag row index was outside its table");
