@@ -647,3 +647,35 @@ def test_bf16_persistent_last_wave_split_bitwise(pool, tile):
         assert c["ok"], c
     finally:
         f.release()
+
+
+@pytest.mark.parametrize("dtype,dim", [("f32", 32), ("bf16", 64), ("f32", 64), ("bf16", 128)])
+def test_claimed_gather_work_resets_between_batches(pool, dtype, dim):
+    """The runtime's gather claims its work from per-slot counters that the launch's
+    last block resets: back-to-back fused batches of very different sizes on one
+    handle (a batch with fewer bags than resident warps, a long one, the short one
+    again) each equal the same invocations run alone."""
+    torch = _torch()
+    # 128-byte rows (one bag per warp, single bags or runs) and 256-byte rows (fp32:
+    # lane groups, four bags per claim; bf16: runs of up to 8 bags)
+    spec = workload.spec_tiny(key="rt_claims_%s_%d" % (dtype, dim), dtype=dtype, n_tables=4, rows=3000, dim=dim,
+                              bot=(128, 64), top=(128, 64, 1), l_min=0, l_max=60)
+    fn = prepare(pool, spec, max_batch=4000)
+    try:
+        plans = [[3, 1], [1500, 700, 0, 999], [3, 1], [2, 2, 2], [1500, 700, 0, 999]]
+        for k, sizes in enumerate(plans):
+            invs = [workload.make_invocation(spec, B, seed=1400 + 10 * k + i) for i, B in enumerate(sizes)]
+            fused = [DevInvocation(v) for v in invs]
+            alone = [DevInvocation(v) for v in invs]
+            fn.invoke_batch([d.args() for d in fused])
+            for d in alone:
+                fn.invoke(*d.args())
+            torch.cuda.synchronize()
+            for a, b in zip(fused, alone):
+                assert torch.equal(a.out[:a.batch], b.out[:b.batch]), (k, a.batch)
+                assert not torch.isnan(a.out[:a.batch]).any()
+        fn.check_errors()
+        w = workload.weights_arrays(spec)
+        _check_inv(spec, w, fused[0], RTOL[dtype])
+    finally:
+        fn.release()
