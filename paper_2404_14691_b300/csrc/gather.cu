@@ -1,7 +1,10 @@
 // Embedding-bag gather-sum over a fused batch of invocations (HBM-bound).
 //
-// Each warp owns one bag at a time (grid-stride over the T*M bags of the batch,
-// table-major so that neighbouring warps read the same table).  A row of the
+// Each warp owns one bag at a time (the T*M bags of the batch in table-major order,
+// so that neighbouring warps read the same table; a warp's bags are a fixed
+// grid-stride share, or -- with GatherArgs::work -- claimed from a counter as it
+// goes, which balances bags of uneven length and lets blocks that start early take
+// more).  A row of the
 // table is LPR lanes x 16 bytes; a warp therefore reads RPW = 32/LPR rows per
 // load instruction and keeps U such instructions in flight.  Row indices are
 // fetched 32 at a time with one coalesced load and broadcast with shuffles.
@@ -122,9 +125,10 @@ __device__ __forceinline__ void finish_bag(float (&acc)[VPL][BF16 ? 8 : 4], cons
   }
 }
 
-// Grid-stride over runs of `run` (<= RUN) consecutive bags (table-major: consecutive
-// rows of one table, moving to the next table after row M - 1), calling
-// bag_sum(t, r, i) for table t, batch row r of invocation i.  Inside a run the table,
+// Walk runs of `run` (<= RUN) consecutive bags (table-major: consecutive rows of one
+// table, moving to the next table after row M - 1), claimed one run at a time from
+// `work` or, without it (or beyond 32-bit bag arithmetic), as a fixed grid-stride
+// share, calling bag_sum(t, r, i) for table t, batch row r of invocation i.  Inside a run the table,
 // the row and its invocation advance incrementally, so the division and the
 // invocation search happen once per run; 32-bit index arithmetic whenever the bag
 // count allows it (a 64-bit division is a long instruction sequence).  RUN = 1
