@@ -307,6 +307,8 @@ cudaError_t launch_one(const GatherArgs& a, const InvTable& tab, cudaStream_t s)
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(gather_kernel<BF16, LPR, VPL, U, RUN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxL1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_kernel<BF16, LPR, VPL, U, RUN>, 256, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
@@ -468,6 +470,8 @@ cudaError_t launch_group(const GatherArgs& a, const InvTable& tab, cudaStream_t 
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(gather_group_kernel<BF16, LPR, VPL, U>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxL1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_group_kernel<BF16, LPR, VPL, U>, 256, 0);
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
