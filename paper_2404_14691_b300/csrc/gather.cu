@@ -481,7 +481,9 @@ cudaError_t launch_group(const GatherArgs& a, const InvTable& tab, cudaStream_t 
   int64_t need = (bags + 8 * NG - 1) / (8 * NG);
   int64_t grid = static_cast<int64_t>(sms) * blocks_per_sm;
   if (need < grid) grid = need;
-  if (bags + grid * 8 * NG >= (int64_t(1) << 32)) return cudaErrorInvalidValue;  // 32-bit bag arithmetic
+  // 32-bit bag arithmetic: a warp's last claim (or grid-stride step) ends at most one
+  // unit of NG bags beyond the grid's warps' share past the last bag
+  if (bags + (grid * 8 + 1) * NG >= (int64_t(1) << 32)) return cudaErrorInvalidValue;
   gather_group_kernel<BF16, LPR, VPL, U><<<static_cast<unsigned>(grid), 256, 0, s>>>(a, tab);
   count_launch();
   return cudaGetLastError();
