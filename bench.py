@@ -864,7 +864,7 @@ def _share_client(mode, path, which, q):
 
 def run_share(args):
     """Cold-process setup when the read-only data belongs to another process (the
-    paper's daemon, Sec. 4.1): a fresh function process staging itself, attaching
+    paper's daemon, Sec. 4.1 and Sec. 5.1): a fresh function process staging itself, attaching
     to an owner that stages on request (its staging overlaps the new process's
     context creation), and attaching to an owner that already holds the key."""
     import torch.multiprocessing as mp

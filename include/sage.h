@@ -4,21 +4,27 @@
  * function's read-only data (SAGE, arXiv 2404.14691).
  *
  * Paper mapping
- *   - Request / Data{key, Type ReadOnly|Writable, data_dptr} (Sec. 4.1, Sec. 5.2):
- *     sage_fn_desc / sage_data_desc / sage_access.
+ *   - Request / Data{key, Type ReadOnly|Writable, data_dptr} (Sec. 4.2, Sec. 5.1,
+ *     Sec. 6.2): sage_fn_desc / sage_data_desc / sage_access.
  *   - Unified memory daemon, one per GPU, that loads data proactively and hands
- *     out device addresses (Sec. 3 overview, Sec. 4.1): sage_pool.
+ *     out device addresses (Sec. 4.1, Sec. 5.1): sage_pool.
  *   - Parallelised function setup: GPU data preparation runs beside the context /
- *     module / workspace setup (Sec. 4.1, stages 3||4 and 5||6 of fig. workflow):
+ *     module / workspace setup (Sec. 5.1, stages 3||4 and 5||6 of fig. workflow):
  *     sage_prepare returns at once; staging runs on the pool's side stream and
  *     host producer threads while the calling thread loads kernels and builds the
  *     workspace.
  *   - SageLoadToGPU returns the pointer before the data is ready; the kernel
- *     executor checks readiness before launch (Sec. 4.2): sage_invoke makes the
- *     launch stream wait on the data's ready event.
- *   - Read-only memory sharing (Sec. 5.2): a second sage_prepare of the same key
+ *     executor checks readiness before launch (Sec. 5.2): sage_invoke makes the
+ *     launch stream wait on the data's ready event; sage_wait is the host-side
+ *     form of the same check.
+ *   - Read-only memory sharing (Sec. 6.2): a second sage_prepare of the same key
  *     takes a reference to the resident copy and loads nothing.
- *   - Context memory sharing (Sec. 5.4): every invocation of a function runs in
+ *   - Multi-stage resource exit (Sec. 6.3): sage_release frees (or, with a host
+ *     cache, demotes to host memory) a key's read-only data after its last
+ *     reference; sage_pool_destroy ends the daemon.
+ *   - Memory taxonomy (Sec. 6.1, Table tb:memory): sage_pool_stats separates the
+ *     read-only bytes from the workspaces (writable memory).
+ *   - Context memory sharing (Sec. 6.4): every invocation of a function runs in
  *     one process / one CUDA context and reuses its kernels and workspace.
  *
  * The GPU function (the workload this runtime executes; the paper names no
@@ -63,7 +69,7 @@ typedef enum {
     SAGE_ERR_DEVICE = -8       /* a kernel's bounded wait ran out (reported by sage_fn_check) */
 } sage_status;
 
-/* Data.Type of the paper (Sec. 5.2): read-only data is shared between invocations. */
+/* Data.Type of the paper (Sec. 6.2): read-only data is shared between invocations. */
 typedef enum { SAGE_READONLY = 0, SAGE_WRITABLE = 1 } sage_access;
 
 /* Element type of the function's tables and weights.  SAGE_F32: fp32 tables,
@@ -90,7 +96,7 @@ typedef struct {
     sage_dev_alloc_fn dev_alloc;   /* optional */
     sage_dev_free_fn dev_free;     /* optional; set both or neither */
     void* alloc_ctx;
-    size_t host_cache_bytes;       /* stage 2 of the multi-stage exit (Sec. 5.3): when the last
+    size_t host_cache_bytes;       /* stage 2 of the multi-stage exit (Sec. 6.3): when the last
                                       reference of a key is released, its read-only data is kept in
                                       page-locked host memory (up to this many bytes, least recently
                                       used images evicted) and a later prepare of the key re-stages
@@ -111,9 +117,9 @@ typedef struct {
  * Returns 0 on success, nonzero on failure (the item becomes sticky-failed). */
 typedef int (*sage_fill_fn)(void* dst, size_t offset, size_t bytes, void* ctx);
 
-/* One data item of a request (Data of Sec. 4.1 / 5.2).  Exactly one of host_src
+/* One data item of a request (Data of Sec. 5.1 / 6.2).  Exactly one of host_src
  * or fill must be set.  The caller keeps host_src (or fill_ctx) alive until
- * sage_fn_wait returns SAGE_OK for a handle of this key (or the handle fails). */
+ * sage_wait returns SAGE_OK for a handle of this key (or the handle fails). */
 typedef struct {
     const char* key;               /* unused for the two items of sage_fn_desc (the fn_key names both) */
     sage_access access;            /* must be SAGE_READONLY for tables and weights */
@@ -167,7 +173,7 @@ typedef struct {
 } sage_invocation;
 
 /* The same invocation with HOST buffers (Writable data loaded to the GPU and the
- * result dumped back, SageLoadToGPU / SageDumpToDB of Sec. 4.2). */
+ * result dumped back, SageLoadToGPU / SageDumpToDB of Sec. 5.2). */
 typedef struct {
     int batch;
     const float* dense;            /* host [B, n_dense] */
@@ -197,25 +203,28 @@ typedef struct {
     int64_t host_cache_entries;
     int64_t host_cache_hits;       /* prepares re-staged from the host cache */
     int64_t demotions;             /* releases that moved read-only data to the host cache */
-} sage_pool_stats;
+} sage_pool_stats_t;
 
 /* Create a pool on config->device: makes the CUDA context current, creates the
- * side (staging) stream, the pinned staging ring and the producer threads
- * (the paper's "unified memory daemon", one per GPU).  config may be NULL. */
+ * side (staging) stream, the pinned staging ring and the producer threads.
+ * Paper: the unified memory daemon, one per GPU (Sec. 4.1), set up by SageInit
+ * (Sec. 4.2).  config may be NULL (defaults).  On failure *out is untouched;
+ * SAGE_ERR_CUDA when the device or its context cannot be set up. */
 sage_status sage_pool_create(const sage_pool_config* config, sage_pool* out);
 
 /* Prepare function desc->fn_key and return a new reference in *out.
- * Resident key: takes a reference (no data loaded) -- read-only sharing, Sec. 5.2.
+ * Resident key: takes a reference (no data loaded) -- read-only sharing, Sec. 6.2.
  * New key: reserves budget (SAGE_ERR_NOMEM if over), allocates the device copy,
  * queues the staging of tables and weights, then -- on the calling thread, while
- * staging runs -- loads the kernels and allocates the workspace (Sec. 4.1).
+ * staging runs -- loads the kernels and allocates the workspace (the engine's
+ * context preparation beside the daemon's data preparation, Sec. 5.1).
  * Returns without waiting for the data.  A resident key re-prepared with another
  * dtype, shape or byte size returns SAGE_ERR_INVALID. */
 sage_status sage_prepare(sage_pool pool, const sage_fn_desc* desc, sage_fn* out);
 
-/* Device addresses of the function's read-only items (data_dptr of Sec. 4.1 /
- * SageLoadToGPU of Sec. 4.2): valid while the handle lives; the bytes are there
- * only once sage_fn_query / sage_fn_wait return SAGE_OK (kernels launched by
+/* Device addresses of the function's read-only items (data_dptr of Sec. 5.1 /
+ * SageLoadToGPU of Sec. 5.2): valid while the handle lives; the bytes are there
+ * only once sage_fn_query / sage_wait return SAGE_OK (kernels launched by
  * sage_invoke* wait for them on the device).  Either output may be NULL. */
 sage_status sage_fn_data(sage_fn fn, const void** tables, const void** weights);
 
@@ -223,12 +232,19 @@ sage_status sage_fn_data(sage_fn fn, const void** tables, const void** weights);
  * SAGE_PENDING while staging, SAGE_ERR_STAGING after a producer failure. */
 sage_status sage_fn_query(sage_fn fn);
 
-/* Wait until the read-only data is on the device.  timeout_us < 0 waits forever.
- * Returns SAGE_OK, SAGE_ERR_TIMEOUT or SAGE_ERR_STAGING. */
-sage_status sage_fn_wait(sage_fn fn, int64_t timeout_us);
+/* Wait on the host until the function's read-only data is on the device.
+ * Paper: SageLoadToGPU hands out the pointer before the data has arrived, and
+ * the kernel executor asks the daemon whether the data is ready before it
+ * launches (Sec. 5.2); sage_fn_data is the first half, this call the host-side
+ * form of the second (sage_invoke* need not call it: they make the device wait).
+ * timeout_us < 0 waits forever.  Returns SAGE_OK, SAGE_ERR_TIMEOUT (the data is
+ * still being staged; the handle stays usable) or SAGE_ERR_STAGING (the producer
+ * failed; sticky); SAGE_ERR_INVALID for a bad handle. */
+sage_status sage_wait(sage_fn fn, int64_t timeout_us);
 
-/* Run one invocation on `stream` (asynchronous).  The stream first waits, on the
- * device, for the read-only data (the executor's readiness check, Sec. 4.2); the
+/* Run one invocation on `stream` (asynchronous): SageRun of Sec. 4.2 for one
+ * request.  The stream first waits, on the device, for the read-only data (the
+ * executor's readiness check, Sec. 5.2); the
  * calling thread blocks only until the last staging copy has been queued.
  * Returns SAGE_ERR_STAGING if the data failed to load. */
 sage_status sage_invoke(sage_fn fn, const sage_invocation* inv, void* stream);
@@ -236,7 +252,8 @@ sage_status sage_invoke(sage_fn fn, const sage_invocation* inv, void* stream);
 /* Run n invocations of the same function as ONE fused batch of sum(batch) samples
  * on `stream`: one launch per layer / gather over all of them, outputs written to
  * each invocation's own `out`.  Each result equals (bitwise) the result of
- * invoking it alone. */
+ * invoking it alone.  The paper has no counterpart (batching is this library's
+ * addition); n in [1, 256], the buffers of every invocation as for sage_invoke. */
 sage_status sage_invoke_batch(sage_fn fn, const sage_invocation* invs, int n, void* stream);
 
 /* sage_invoke_batch with host buffers: copies each invocation's inputs to the
@@ -257,15 +274,24 @@ sage_status sage_invoke_batch_host_async(sage_fn fn, const sage_host_invocation*
  * skipped) or SAGE_ERR_DEVICE (a kernel's bounded wait ran out). */
 sage_status sage_fn_check(sage_fn fn);
 
-/* Drop a reference.  When the last reference of a key is dropped, the pool waits
- * for the key's in-flight work, frees its device copy and workspace and returns
- * the budget (the paper's release after the last invocation, Sec. 5.3). */
+/* Drop a reference (the handle is invalid afterwards).  When the last reference
+ * of a key is dropped, the pool waits for the key's in-flight work, frees its
+ * device copy and workspace and returns the budget -- or, with host_cache_bytes,
+ * first keeps the read-only data in host memory: the first two stages of the
+ * paper's multi-stage resource exit (Sec. 6.3).  SAGE_ERR_INVALID for a bad
+ * handle. */
 sage_status sage_release(sage_fn fn);
 
-/* Destroy an empty pool; SAGE_ERR_BUSY while any reference is live. */
+/* Destroy an empty pool: the daemon's end, after every function it served has
+ * exited (the last stage of Sec. 6.3).  SAGE_ERR_BUSY while any reference is
+ * live (nothing is freed then); the host cache is freed. */
 sage_status sage_pool_destroy(sage_pool pool);
 
-sage_status sage_pool_stats_get(sage_pool pool, sage_pool_stats* out);
+/* Copy the pool's counters into *out.  Read-only bytes and workspace bytes are
+ * counted apart, the paper's split of a function's memory into read-only,
+ * writable and context memory (Sec. 6.1, Table tb:memory); H2D bytes count each
+ * shared key once (Sec. 6.2).  SAGE_ERR_INVALID for a NULL argument. */
+sage_status sage_pool_stats(sage_pool pool, sage_pool_stats_t* out);
 
 /* Page-locked host memory for invocation buffers and host images: 2 MiB aligned,
  * backed by transparent huge pages where the kernel allows, registered with
@@ -276,7 +302,8 @@ sage_status sage_pool_stats_get(sage_pool pool, sage_pool_stats* out);
 sage_status sage_host_alloc(size_t bytes, void** out);
 sage_status sage_host_free(void* ptr);
 
-/* Thread-local message of the last error returned on this thread ("" if none). */
+/* Thread-local message of the last error returned on this thread ("" if none).
+ * The paper has no counterpart (status codes replace exceptions at the boundary). */
 const char* sage_last_error(void);
 
 /* Number of kernels the library has launched in this process (all pools). */
@@ -327,14 +354,14 @@ sage_status sage_tuning_load(const char* path);
  * pool's GPU with continuous batching (the project's serving form; the paper's
  * evaluation replays a trace of function requests, Sec. 7.1).  Each function is
  * prepared when its first request arrives (cold setup: staging beside kernel
- * loading, Sec. 4.1) and its requests queue until its data is ready.  Admission
+ * loading, Sec. 5.1) and its requests queue until its data is ready.  Admission
  * is by device memory: a prepare that exceeds the pool budget evicts idle
  * resident functions (least recently used first) or waits.  Every function owns
  * lanes_per_fn streams, each with its own workspace slot; an idle lane takes ALL
  * queued requests of its function (up to the batch limits) as one fused batch,
  * so requests arriving while others run join the next batch, and lanes of
  * different functions overlap on the device.  An idle function keeps its data
- * for linger_s (stage 1 of the multi-stage exit, Sec. 5.3), then is released.
+ * for linger_s (stage 1 of the multi-stage exit, Sec. 6.3), then is released.
  * Request buffers are host memory (pinned recommended): inputs are copied in and
  * outputs copied back inside each batch.  Latency = completion - arrival. */
 typedef struct {
@@ -392,12 +419,28 @@ sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n_fns, const
  * needed.  It calls no allocator (no cudaMalloc/cudaMallocAsync/cudaFree, no
  * library routine that allocates).  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  All calls share the array and it
- * keeps the last call's contents: calls whose kernels overlap on the GPU race,
- * so issue them on one stream (or order them).  Out-of-range bag rows are
- * skipped; the error word is not reported.  Asynchronous on `stream`. */
+ * that first call before any stream capture.  The address is cached for the
+ * life of the process: resetting the device after the first call is not
+ * supported.  All calls share the array and it keeps the last call's contents:
+ * calls whose kernels overlap on the GPU race, so issue them on one stream (or
+ * order them).  Alignment: tables and weights 256 bytes, dense and out 16 bytes,
+ * indices 4 bytes, offsets 8 bytes; a misaligned pointer is refused with
+ * SAGE_ERR_INVALID before anything is launched.  Out-of-range bag rows are
+ * skipped, and a tensor-core GEMM whose bounded wait runs out leaves its output
+ * wrong; both set the array's error word, which each call clears first and
+ * sage_noalloc_check reports.  Asynchronous on `stream`. */
 sage_status sage_invoke_noalloc(const sage_fn_desc* shape, const void* tables, const void* weights,
                                 const sage_invocation* inv, void* stream);
+
+/* Error report of the no-allocation entry point on the current device: waits for
+ * `stream` (the stream of the calls to check), reads the shared error word into
+ * host memory and clears it (no allocation).  Returns SAGE_OK, SAGE_ERR_BOUNDS (a
+ * bag row index was outside its table; that row was skipped) or SAGE_ERR_DEVICE
+ * (a kernel's bounded wait ran out; the outputs of that call are not valid).
+ * Every call clears the word when it starts, so the report covers the last call
+ * on `stream`: check after each call whose errors matter.  The paper has no
+ * counterpart. */
+sage_status sage_noalloc_check(void* stream);
 
 /* ---- building blocks (the kernels of sage_invoke, callable one by one) ----
  * Used by the parity tests and the kernel benchmarks.  All pointers are device
@@ -437,8 +480,8 @@ sage_status sage_linear_tiled(sage_dtype dtype, int M, int N, int K, const void*
  *
  * The paper's memory daemon is a separate process: a function's engine hands it
  * the data request first, and the daemon loads the data while the engine creates
- * the GPU context, the two in parallel (Sec. 3.1, Sec. 4.1); all invocations of a
- * function on a GPU share the daemon's one read-only copy (Sec. 5.2).  Here:
+ * the GPU context, the two in parallel (Sec. 4.1, Sec. 5.1); all invocations of a
+ * function on a GPU share the daemon's one read-only copy (Sec. 6.2).  Here:
  *
  *   owner process : pool created with exportable = 1; sage_share_start serves the
  *                   functions given to sage_share_register on a UNIX socket;

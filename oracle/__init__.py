@@ -10,7 +10,7 @@ Contents
   * pack_invocations: the plain definition of fusing several invocations of one
     function into one batch (concatenate samples; rebase each table's CSR
     offsets by the running index count).
-  * PoolModel: the refcount / budget model of read-only sharing (Sec. 5.2 of the
+  * PoolModel: the refcount / budget model of read-only sharing (Sec. 6.2 of the
     paper: read-only data is loaded on the first invocation and shared by the
     concurrent ones; it is released when no invocation holds it).
   * check_close: the componentwise tolerance used by every parity test.
@@ -248,7 +248,7 @@ def pack_invocations(invs: Sequence[dict], n_tables: int) -> dict:
 # ---------------------------------------------------------------- sharing model
 
 class PoolModel:
-    """Refcount/budget model of read-only sharing (Sec. 5.2).
+    """Refcount/budget model of read-only sharing (Sec. 6.2).
 
     The first prepare of a key loads its bytes (counted as H2D bytes) if the
     budget allows; later prepares of a resident key only take a reference;
@@ -331,7 +331,7 @@ def check_output(got, ref, mag, rtol: float) -> dict:
 # ---------------------------------------------------------------- setup-time model
 
 def setup_latency_model(stages: Dict[str, float], parallel: bool = True) -> float:
-    """End-to-end latency of one invocation from its stage durations (Sec. 4.1).
+    """End-to-end latency of one invocation from its stage durations (Sec. 5.1).
 
     Serial setup runs every stage one after another.  The parallelised setup
     runs GPU-context preparation beside data preparation (CPU data, then GPU

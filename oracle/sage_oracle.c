@@ -6,7 +6,7 @@
  * no code with the CUDA path.
  *
  * The paper (SAGE, arXiv 2404.14691) does not define the GPU function itself: its
- * mechanisms (parallelised setup, Sec. 4; read-only memory sharing, Sec. 5.2)
+ * mechanisms (parallelised setup, Sec. 5; read-only memory sharing, Sec. 6.2)
  * produce exactly the result of running each invocation on its own.  So the
  * oracle computes, for every invocation independently, the plain definition of
  * the synthetic recommendation-style function:

@@ -160,7 +160,7 @@ class Function:
         return check(lib().sage_fn_query(self.handle), "sage_fn_query")
 
     def wait(self, timeout_us: int = -1) -> None:
-        check(lib().sage_fn_wait(self.handle, int(timeout_us)), "sage_fn_wait")
+        check(lib().sage_wait(self.handle, int(timeout_us)), "sage_wait")
 
     def invoke(self, batch: int, dense: int, indices: int, offsets: int, out: int, stream=None,
                num_indices: int = 0) -> None:
@@ -240,7 +240,7 @@ class Pool:
 
     def stats(self) -> dict:
         s = PoolStats()
-        check(lib().sage_pool_stats_get(self.handle, ctypes.byref(s)), "sage_pool_stats_get")
+        check(lib().sage_pool_stats(self.handle, ctypes.byref(s)), "sage_pool_stats")
         return {name: getattr(s, name) for name, _ in PoolStats._fields_}
 
     def destroy(self) -> None:

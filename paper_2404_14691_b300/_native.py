@@ -109,7 +109,7 @@ SIGNATURES = [
     ("sage_prepare", _i, [_vp, ctypes.POINTER(FnDesc), ctypes.POINTER(_vp)]),
     ("sage_fn_data", _i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     ("sage_fn_query", _i, [_vp]),
-    ("sage_fn_wait", _i, [_vp, _i64]),
+    ("sage_wait", _i, [_vp, _i64]),
     ("sage_invoke", _i, [_vp, ctypes.POINTER(Invocation), _vp]),
     ("sage_invoke_batch", _i, [_vp, ctypes.POINTER(Invocation), _i, _vp]),
     ("sage_invoke_batch_host", _i, [_vp, ctypes.POINTER(HostInvocation), _i, _vp]),
@@ -117,7 +117,7 @@ SIGNATURES = [
     ("sage_fn_check", _i, [_vp]),
     ("sage_release", _i, [_vp]),
     ("sage_pool_destroy", _i, [_vp]),
-    ("sage_pool_stats_get", _i, [_vp, ctypes.POINTER(PoolStats)]),
+    ("sage_pool_stats", _i, [_vp, ctypes.POINTER(PoolStats)]),
     ("sage_last_error", ctypes.c_char_p, []),
     ("sage_host_alloc", _i, [_sz, ctypes.POINTER(_vp)]),
     ("sage_host_free", _i, [_vp]),
@@ -131,6 +131,7 @@ SIGNATURES = [
     ("sage_serve", _i, [_vp, ctypes.POINTER(FnDesc), _i, ctypes.POINTER(Request), _i, ctypes.POINTER(ServeConfig),
                         ctypes.POINTER(RequestResult), ctypes.POINTER(ServeStats)]),
     ("sage_invoke_noalloc", _i, [ctypes.POINTER(FnDesc), _vp, _vp, ctypes.POINTER(Invocation), _vp]),
+    ("sage_noalloc_check", _i, [_vp]),
     ("sage_embedding_bag_sum", _i, [_i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _i, _vp, _vp]),
     ("sage_linear", _i, [_i, _i, _i, _i, _vp, _i, _vp, _vp, _i, _vp, _i, _vp, _vp]),
     ("sage_share_start", _i, [_vp, ctypes.c_char_p, ctypes.POINTER(_vp)]),

@@ -136,7 +136,7 @@ void preload_bottom01_kernels();
 // ---------------------------------------------------------------- cross-process sharing
 //
 // The read-only copy of a function can live in one process (the owner, whose pool
-// was created exportable) and be mapped by others (Sec. 4.1: the data is prepared
+// was created exportable) and be mapped by others (Sec. 5.1: the data is prepared
 // by a daemon process while the function process sets up its own context).  The
 // owner allocates that copy as virtual-memory-management (VMM) physical memory
 // that can be exported as a POSIX file descriptor; a client imports the

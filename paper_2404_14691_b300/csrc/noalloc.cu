@@ -16,8 +16,14 @@
 // array's name as a device address (on the host it names a stand-in), so the
 // first call on each device looks the address up with cudaGetSymbolAddress,
 // with that device current, and caches it; make that first call before any
-// stream capture.  All calls share the one array: a call overwrites the last
-// call's contents, and two calls whose kernels overlap on the GPU race.
+// stream capture.  The cached address belongs to the device's context as it was
+// then: resetting the device (cudaDeviceReset) after the first call is not
+// supported.  All calls share the one array: a call overwrites the last call's
+// contents, and two calls whose kernels overlap on the GPU race.
+//
+// Errors the kernels find (a bag row outside its table, skipped; a tensor-core
+// GEMM's bounded wait that ran out) land in the array's error word, which every
+// call clears first; sage_noalloc_check reads it back and clears it.
 #include <stdint.h>
 #include <stdio.h>
 
@@ -44,6 +50,30 @@ sage_status noalloc_fail(sage_status st, const char* msg) {
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// The scratch address of the current device, looked up (once per device, with
+// that device current) on first use.  *dev receives the device ordinal.
+sage_status scratch_base(char** out, int* dev_out) {
+  char msg[160];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return noalloc_fail(SAGE_ERR_CUDA, "cudaGetDevice failed");
+  std::lock_guard<std::mutex> g(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return noalloc_fail(SAGE_ERR_CUDA, msg);
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<char*>(g_scratch_ptr[dev]);
+  if (dev_out) *dev_out = dev;
+  return SAGE_OK;
+}
+
 }  // namespace
 
 extern "C" sage_status sage_invoke_noalloc(const sage_fn_desc* shape, const void* tables, const void* weights,
@@ -69,6 +99,15 @@ extern "C" sage_status sage_invoke_noalloc(const sage_fn_desc* shape, const void
   if (B == 0) return SAGE_OK;
   if (!inv->dense || !inv->indices || !inv->offsets || !inv->out)
     return noalloc_fail(SAGE_ERR_INVALID, "null invocation buffer");
+  // the kernels read table rows and weights with 16-byte loads and TMA (weight
+  // offsets are 256-byte aligned relative to the item), dense rows and outputs
+  // with vector accesses: a misaligned buffer is refused here, before any launch
+  if (!aligned(tables, 256) || !aligned(weights, 256))
+    return noalloc_fail(SAGE_ERR_INVALID, "tables and weights must be 256-byte aligned");
+  if (!aligned(inv->dense, 16) || !aligned(inv->out, 16))
+    return noalloc_fail(SAGE_ERR_INVALID, "dense and out must be 16-byte aligned");
+  if (!aligned(inv->indices, 4) || !aligned(inv->offsets, 8))
+    return noalloc_fail(SAGE_ERR_INVALID, "indices must be 4-byte and offsets 8-byte aligned");
 
   // layers (in, out) and their places inside the weights item
   const int nb = d.n_bot, nt = d.n_top;
@@ -117,23 +156,8 @@ extern "C" sage_status sage_invoke_noalloc(const sage_fn_desc* shape, const void
   }
 
   // per-device set-up: the array's device address, looked up with the device current
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return noalloc_fail(SAGE_ERR_CUDA, "cudaGetDevice failed");
   char* base = nullptr;
-  {
-    std::lock_guard<std::mutex> g(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        snprintf(msg, sizeof(msg), "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        return noalloc_fail(SAGE_ERR_CUDA, msg);
-      }
-      g_scratch_ptr[dev] = p;
-    }
-    base = static_cast<char*>(g_scratch_ptr[dev]);
-  }
+  if (sage_status st = scratch_base(&base, nullptr); st != SAGE_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream_);
   int* err = reinterpret_cast<int*>(base);
   if (cudaMemsetAsync(err, 0, kErrBytes, s) != cudaSuccess) return noalloc_fail(SAGE_ERR_CUDA, "memset");
@@ -207,5 +231,20 @@ extern "C" sage_status sage_invoke_noalloc(const sage_fn_desc* shape, const void
     snprintf(msg, sizeof(msg), "kernel launch: %s", cudaGetErrorString(e));
     return noalloc_fail(e == cudaErrorInvalidValue ? SAGE_ERR_INVALID : SAGE_ERR_CUDA, msg);
   }
+  return SAGE_OK;
+}
+
+extern "C" sage_status sage_noalloc_check(void* stream_) {
+  char* base = nullptr;
+  if (sage_status st = scratch_base(&base, nullptr); st != SAGE_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream_);
+  int w = 0;
+  // a plain copy into a host int and a memset: no allocation
+  if (cudaMemcpyAsync(&w, base, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess || cudaMemsetAsync(base, 0, sizeof(int), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return noalloc_fail(SAGE_ERR_CUDA, "reading the no-alloc error word failed");
+  if (w & sage::kErrTimeout) return noalloc_fail(SAGE_ERR_DEVICE, "a kernel's bounded wait ran out");
+  if (w & sage::kErrBounds) return noalloc_fail(SAGE_ERR_BOUNDS, "a bag row index was outside its table");
   return SAGE_OK;
 }

@@ -1,8 +1,8 @@
 // Runtime behind the C-ABI of include/sage.h: the per-GPU pool (the paper's
-// unified memory daemon, Sec. 3/4.1), read-only sharing by key with reference
-// counts (Sec. 5.2), staging of read-only data through a pinned ring on a side
+// unified memory daemon, Sec. 4.1), read-only sharing by key with reference
+// counts (Sec. 6.2), staging of read-only data through a pinned ring on a side
 // stream while the calling thread loads kernels and builds workspaces
-// (parallelised setup, Sec. 4.1), the readiness gate before launch (Sec. 4.2),
+// (parallelised setup, Sec. 5.1), the readiness gate before launch (Sec. 5.2),
 // and the invocation chain of the recommendation-style function.
 #include <stdarg.h>
 #include <stdio.h>
@@ -309,7 +309,7 @@ struct sage_pool_s {
   size_t host_budget = 0, host_used = 0;
   std::unordered_map<std::string, HostImage> hcache;
   uint64_t hclock = 0;
-  sage_pool_stats st{};
+  sage_pool_stats_t st{};
   std::atomic<int64_t> h2d{0}, invocations{0};
 
   void* dev_alloc(size_t bytes, cudaStream_t s) {
@@ -1456,7 +1456,7 @@ sage_status sage_fn_query(sage_fn f) {
   return fail(SAGE_ERR_CUDA, "cudaEventQuery: %s", cudaGetErrorString(q));
 }
 
-sage_status sage_fn_wait(sage_fn f, int64_t timeout_us) {
+sage_status sage_wait(sage_fn f, int64_t timeout_us) {
   if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
   auto t0 = Clock::now();
   for (;;) {
@@ -1820,10 +1820,10 @@ sage_status sage_pool_destroy(sage_pool P) {
   return SAGE_OK;
 }
 
-sage_status sage_pool_stats_get(sage_pool P, sage_pool_stats* out) {
+sage_status sage_pool_stats(sage_pool P, sage_pool_stats_t* out) {
   if (!P || !out) return fail(SAGE_ERR_INVALID, "null argument");
   std::lock_guard<std::mutex> g(P->mu);
-  sage_pool_stats s = P->st;
+  sage_pool_stats_t s = P->st;
   s.budget_bytes = P->budget;
   s.resident_bytes = P->used;
   s.readonly_bytes = 0;

@@ -2,7 +2,7 @@
 // GPU with continuous batching.
 //
 // Requests arrive at their trace times.  A function is prepared (its read-only
-// data staged, Sec. 4.1) when its first request arrives; while it stages, its
+// data staged, Sec. 5.1) when its first request arrives; while it stages, its
 // requests queue.  Admission is by device memory: a prepare that does not fit the
 // pool budget evicts idle resident functions (least recently used first) and
 // otherwise waits.  Each function owns `lanes` streams, each with its own
@@ -11,7 +11,7 @@
 // requests that arrive while others run are batched as soon as a lane frees up,
 // and the lanes of different functions overlap on the device.  A resident
 // function with nothing queued or in flight keeps its data for `linger_s`
-// (the first stage of the paper's multi-stage exit, Sec. 5.3) and is then
+// (the first stage of the paper's multi-stage exit, Sec. 6.3) and is then
 // released.  With sm_partition each function's lanes are streams of its own SM
 // partition (a green context holding SMs / n_fns SMs), so that one function's
 // batches never occupy another's SMs.

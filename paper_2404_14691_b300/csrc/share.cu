@@ -1,6 +1,6 @@
 // Cross-process sharing of a function's read-only copy (the paper's memory daemon
-// as a separate process, Sec. 3.1 / Sec. 4.1, sharing of read-only data between
-// invocations, Sec. 5.2).
+// as a separate process, Sec. 4.1 / Sec. 5.1, sharing of read-only data between
+// invocations, Sec. 6.2).
 //
 // Owner: a pool created exportable allocates each read-only item as CUDA VMM
 // physical memory with a POSIX file-descriptor handle.  sage_share_start listens
@@ -423,7 +423,7 @@ void sage_share_s::serve(ShareConn* c) {
     // READY once staging has finished (or failed); stop interrupts the wait
     sage_status s;
     do {
-      s = sage_fn_wait(f, 100000);
+      s = sage_wait(f, 100000);
     } while (s == SAGE_ERR_TIMEOUT && !stop.load());
     Msg rd;
     rd.type = sage::kReady;

@@ -1,5 +1,5 @@
 """Bottom layers 0 and 1 of a pre-split fp32 function fused into one kernel: layer 0
-(Sec. 6 workload: 13 dense features into the bottom MLP) is computed straight into
+(13 dense features into the bottom MLP) is computed straight into
 the A tiles of layer 1's tensor-core GEMM.  Every fused tile configuration gives the
 bits of the two separate kernels (bottom0, then the pre-split GEMM), and the
 function still matches the oracle."""

@@ -1,5 +1,5 @@
 """Cross-process sharing on one GPU: an owner process stages a function's read-only
-copy once and other processes map it (Sec. 4.1 daemon process, Sec. 5.2 sharing).
+copy once and other processes map it (Sec. 4.1 / 5.1 daemon process, Sec. 6.2 sharing).
 
 Processes are started with `spawn`; none of their kernels waits on another's."""
 import os
