@@ -3,12 +3,16 @@ sharing one device copy of its read-only data, fused into one batch.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
-Default workload (batching, fp32): the function with 8 tables x 100,000 rows x
-64 fp32, bottom MLP 13-512-256-64, top MLP 576-512-256-1; 64 invocations with
-batch sizes uniform in [1, 512] and bag lengths uniform in [1, 40] (Zipf 1.05
-rows), one shared read-only copy.  One step = one fused batch of the 64
-invocations through the whole path (bottom MLP, gather, top MLP, head).
-Prints one JSON line (rank 0).
+Default workload (precision, BF16): the function with 26 tables x 1,000,000 rows
+x 128 bf16 (6.7 GB read-only), bottom MLP 13-512-256-128, top MLP
+3456-1024-512-256-1; 128 invocations with lognormal batch sizes (median 256, at
+most 4096; ~57k samples) and bag lengths uniform in [1, 100] (Zipf 1.1 rows), one
+shared read-only copy.  One step = one fused batch of the 128 invocations through
+the whole path (bottom MLP, gather, top MLP, head).  The same line carries the
+uniform-index gather control (26 x 4M x 128, no Zipf reuse), the fp32 batching
+workload (64 invocations of 8 x 100,000 x 64 fp32) and the serving workload's
+latencies including setup (2,000 Poisson requests over 4 functions, served vs one
+invocation per launch).  Prints one JSON line (rank 0).
 """
 import argparse
 import json
@@ -52,11 +56,14 @@ def make_workload(name: str, rank: int = 0):
         invs = [workload.make_invocation(spec, 256, seed=workload.sub_seed("c1", "inv", rank) % (1 << 63))]
         desc = "plain-fp32: 1 invocation, B=256, L=20, Zipf(1.05); tables 8x100000x64 fp32"
         return spec, invs, desc
-    if name in ("c3", "c3-uniform", "c3s", "c3s-uniform"):
+    if name in ("c3", "c3-uniform", "c3s", "c3s-uniform", "c3-uniform-4m"):
         small = name.startswith("c3s")
-        spec = workload.spec_c3("c3s_bf16_26x200k_d128", rows=200_000) if small else workload.spec_c3()
+        if name == "c3-uniform-4m":
+            spec = workload.spec_c3("c3u_bf16_26x4m_d128", rows=4_000_000)
+        else:
+            spec = workload.spec_c3("c3s_bf16_26x200k_d128", rows=200_000) if small else workload.spec_c3()
         sizes = workload.batch_sizes_lognormal(128, seed=workload.sub_seed("c3", "sizes", rank))
-        uni = name.endswith("-uniform")
+        uni = "uniform" in name
         invs = [workload.make_invocation(spec, int(B), seed=workload.sub_seed("c3", "inv", rank, i) % (1 << 63),
                                          uniform_rows=uni)
                 for i, B in enumerate(sizes)]
@@ -170,61 +177,188 @@ def traffic_for(kind: str, workload_name: str):
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_rate(spec, invs, budget_s: float, threads: int):
-    """Invocations/s of the fp64 CPU oracle on whole invocations, stopping after
-    about budget_s seconds (at least one invocation)."""
+def oracle_timing(spec, invs, budget_s: float, threads: int, start: int = 0):
+    """The fp64 CPU oracle on whole invocations of the workload, taken in order from
+    invs[start] (cycling), until about budget_s seconds have passed (at least one).
+
+    Returns (invocations_per_s, done, samples, seconds).  Invocations differ in size,
+    so the rate is the oracle's samples per second divided by the workload's mean
+    samples per invocation: the invocations per second it would sustain on this
+    workload's mix, whichever invocations the sample happened to hold.  Both the
+    benchmark line's cpu_baseline and the reference arm use this one function."""
     import oracle
     w = workload.weights_arrays(spec)
     src = lambda t, r: workload.table_rows(spec, t, r)
+    mean_batch = float(np.mean([v["batch"] for v in invs]))
     t0 = time.perf_counter()
-    done = 0
-    samples = 0
-    for v in invs:
+    done = samples = 0
+    k = start
+    while True:
+        v = invs[k % len(invs)]
         oracle.forward(spec, w, v, row_source=src, n_threads=threads, want_pooled=False)
+        k += 1
         done += 1
         samples += v["batch"]
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return done / el, done, samples, el
+    return samples / el / mean_batch, done, samples, el
 
 
-def roofline_of(kind: str, nl: int, tms: float, work: float, peaks: dict, peak_src: str) -> dict:
-    """Achieved rate of one kernel kind (algorithmic work per launch / mean launch time)
-    against its bound: HBM copy rate for the gather, tensor peaks for the GEMMs."""
-    avg_s = tms / nl / 1e3
+def _avg_launch_s(nl, tms):
+    return tms / nl / 1e3
+
+
+def roofline_of(kind: str, nl: int, tms: float, work: float, peaks: dict, peak_src: str,
+                traffic=None) -> dict:
+    """One kernel kind against its bound, from its live launch times (CUDA events on the
+    launching stream) and its algorithmic work per launch.
+
+    Gather: bound HBM.  `achieved` is DRAM bytes per launch (ncu, profiles/traffic.json,
+    only while the kernel's source is the captured one) over the mean launch time, so
+    `frac` is a true HBM fraction; `effective_GBs` is the algorithmic bytes (every row,
+    index, offset and output) over the same time -- under Zipf reuse most rows come
+    from L1/L2, so it can exceed the HBM rate.  GEMMs: algorithmic flops over the mean
+    launch time against the BURST tensor peak (these kernels run for well under a
+    second): measured bf16, and for fp32 as three tf32 products the measured bf16 peak
+    x the nominal tf32/bf16 ratio (1.1/2.25) / 3."""
+    avg_s = _avg_launch_s(nl, tms)
     per_launch = work / nl
+    base = {"kernel": kind, "launches": nl, "avg_launch_ms": round(avg_s * 1e3, 5),
+            "work_per_launch": per_launch}
     if kind == "gather":
         peak = peaks["hbm_gbs"]
-        achieved = per_launch / avg_s / 1e9
-        return {"kernel": kind, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_src + " (hbm_gbs copy)"}
+        r = dict(base, bound="hbm", unit="GB/s", peak=peak, traffic=traffic,
+                 effective_GBs=round(per_launch / avg_s / 1e9, 1),
+                 effective_over_hbm=round(per_launch / avg_s / 1e9 / peak, 4),
+                 peak_source=peak_src + " (hbm_gbs copy)")
+        if traffic:
+            ach = traffic / avg_s / 1e9
+            r.update(achieved=round(ach, 1), frac=round(ach / peak, 4),
+                     achieved_basis="DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                    "on this kernel source) / live mean launch time")
+        else:
+            r.update(achieved=None, frac=None,
+                     achieved_basis="no DRAM capture of this kernel source: see effective_GBs")
+        return r
     if kind == "gemm_tc":
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+        peak = peaks["bf16_tflops"]
         achieved = per_launch / avg_s / 1e12
-        return {"kernel": kind, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "peak_source": peak_src + " (bf16_tflops_sustained)"}
+        return dict(base, bound="tensor", achieved=round(achieved, 2), peak=peak, unit="TFLOP/s",
+                    frac=round(achieved / peak, 4), traffic=traffic,
+                    peak_source=peak_src + " (bf16_tflops, burst)")
     if kind in ("gemm_tf32x3", "bottom01"):
-        # fp32 on the tensor cores as three tf32 products: the ceiling for useful fp32
-        # flops is the tf32 peak / 3; tf32 peak = measured bf16 x nominal tf32/bf16 (1.1/2.25).
         # (bottom01's flops include its layer 0, ~5% of them, which runs on the FP32 pipes)
-        tf32 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * (1.1 / 2.25)
-        peak = tf32 / 3.0
+        peak = peaks["bf16_tflops"] * (1.1 / 2.25) / 3.0
         achieved = per_launch / avg_s / 1e12
-        return {"kernel": kind, "bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "peak_source": peak_src + " bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (three tf32 "
-                               "products per fp32 product)"}
+        return dict(base, bound="tensor", achieved=round(achieved, 2), peak=round(peak, 1), unit="TFLOP/s",
+                    frac=round(achieved / peak, 4), traffic=traffic,
+                    peak_source=peak_src + " bf16_tflops (burst) x 1.1/2.25 (tf32) / 3 (three tf32 products "
+                                           "per fp32 product)")
     mhz = peaks.get("sm_max_mhz", 2032.0)
     peak = SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
     achieved = per_launch / avg_s / 1e12
-    return {"kernel": kind, "bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 2),
-            "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-            "peak_source": "148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz}
+    return dict(base, bound="alu", achieved=round(achieved, 2), peak=round(peak, 2), unit="TFLOP/s",
+                frac=round(achieved / peak, 4), traffic=traffic,
+                peak_source="148 SMs x 128 FP32 lanes x 2 flop x %.0f MHz (max SM clock)" % mhz)
 
 
 # ------------------------------------------------------------------ our arm
+
+def timed_steps(torch, stream, flush, step, k):
+    """k steps on `stream`, each bracketed by CUDA events on that stream, with the L2
+    flushed (a 256 MiB write) before each, outside the events.  Returns ms per step."""
+    evs = []
+    with torch.cuda.stream(stream):
+        for _ in range(k):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def fused_batch_summary(args, name, dev, plain=False):
+    """One workload's fused batch on its own pool: invocations/s over timed steps (L2
+    flushed between them), optionally the plain one-launch-chain-per-invocation form,
+    and every kernel kind's live time and roofline from a second pass of the same steps."""
+    import torch
+    import paper_2404_14691_b300 as sage
+    spec, invs, desc = make_workload(name)
+    M = int(sum(v["batch"] for v in invs))
+    pool = sage.Pool(device=dev, graphs=True)
+    fn = pool.prepare(**workload.prepare_kwargs(spec), max_batch=max(4096, M), workspace_slots=2)
+    d_inputs = []
+    for v in invs:
+        d = {k: torch.from_numpy(v[k]).cuda() for k in ("dense", "indices", "offsets")}
+        d["out"] = torch.empty(v["batch"], dtype=torch.float32, device="cuda")
+        d_inputs.append(d)
+    fn.wait()
+    if not args.no_autotune:
+        fn.autotune(M)
+    args_all = [(v["batch"], d["dense"].data_ptr(), d["indices"].data_ptr(), d["offsets"].data_ptr(),
+                 d["out"].data_ptr(), v["indices"].size) for v, d in zip(invs, d_inputs)]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    step = lambda: fn.invoke_batch(args_all, stream=stream)
+    for _ in range(args.warmup):
+        step()
+    times = timed_steps(torch, stream, flush, step, args.steps)
+    fn.check_errors()
+    res = {"workload": desc, "invocations_per_step": len(invs), "samples_per_step": M,
+           "lookups_per_step": n_indices(invs),
+           "invocations_per_s": round(len(invs) * len(times) / (sum(times) / 1e3), 2),
+           "ms_per_step": round(sum(times) / len(times), 4), "steps": len(times)}
+    if plain:
+        pstep = lambda: [fn.invoke(*a[:5], stream=stream, num_indices=a[5]) for a in args_all]
+        pstep()
+        pt = timed_steps(torch, stream, flush, pstep, max(3, args.steps // 4))
+        res["plain_invocations_per_s"] = round(len(invs) * len(pt) / (sum(pt) / 1e3), 2)
+        res["speedup_fused_vs_plain"] = round(res["invocations_per_s"] / res["plain_invocations_per_s"], 3)
+    sage.profile_enable(True)
+    sage.profile_read()
+    pt = timed_steps(torch, stream, flush, step, args.steps)
+    sage.profile_enable(False)
+    prof = sage.profile_read()
+    fn.check_errors()
+    peaks, peak_src = load_peaks()
+    res["kernels"] = {k: {"launches": v[0], "ms_per_step": round(v[1] / len(pt), 4)} for k, v in prof.items()}
+    res["rooflines_by_kernel"] = {k: roofline_of(k, nl, tms, work, peaks, peak_src, traffic_for(k, name))
+                                  for k, (nl, tms, work) in prof.items()}
+    fn.release()
+    pool.destroy()
+    del flush, d_inputs
+    torch.cuda.empty_cache()
+    return res
+
+
+def uniform_control(args, dev):
+    """The gather against HBM without cache reuse: the bf16 function with 26 tables x
+    4,000,000 rows x 128 (26.6 GB; each table is 8x the L2) and rows drawn uniformly,
+    the same 128 lognormal invocations.  frac_effective = algorithmic bytes per launch /
+    live launch time / the HBM copy rate; with ~2.9 lookups per row of a 1 GB table
+    per step few rows are found in L2, so this approaches the DRAM fraction (the DRAM
+    bytes of a capture, when one matches the source, give it exactly)."""
+    r = fused_batch_summary(args, "c3-uniform-4m", dev)
+    g = r["rooflines_by_kernel"].get("gather")
+    out = {"workload": r["workload"], "invocations_per_s": r["invocations_per_s"], "ms_per_step": r["ms_per_step"],
+           "gather": g}
+    if g:
+        out["frac_effective"] = g["effective_over_hbm"]
+        out["frac_dram"] = g["frac"]
+    return out
+
+
+def config_of(desc, n_inv, M, nidx, world):
+    """The `config` object of both arms' lines (the same workload, the same keys)."""
+    return {"workload": desc, "invocations_per_step": n_inv, "global_batch": M * world,
+            "lookups_per_step": nidx, "seq_len": None, "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between timed steps (256 MiB write outside the events)"}
+
 
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -304,18 +438,7 @@ def run_ours(args, rank, world, local_rank):
             fn.invoke(*a[:5], stream=stream, num_indices=a[5])
 
     def timed(step, k):
-        evs = []
-        with torch.cuda.stream(stream):
-            for _ in range(k):
-                flush.zero_()
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                step()
-                b.record(stream)
-                evs.append((a, b))
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in evs]
+        return timed_steps(torch, stream, flush, step, k)
 
     dist = None
     if world > 1:
@@ -464,15 +587,14 @@ def run_ours(args, rank, world, local_rank):
     # ---- roofline of the dominant kernel (and of every kernel kind, for the metric's
     # "gather HBM GB/s" and "MLP TC util")
     peaks, peak_src = load_peaks()
-    rooflines = {kind: roofline_of(kind, nl, tms, work, peaks, peak_src) for kind, (nl, tms, work) in prof.items()}
+    rooflines = {kind: roofline_of(kind, nl, tms, work, peaks, peak_src, traffic_for(kind, args.workload))
+                 for kind, (nl, tms, work) in prof.items()}
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
     roof = None
     if dom:
         kind, (nl, tms, work) = dom
         roof = dict(rooflines[kind])
-        roof["traffic"] = traffic_for(kind, args.workload)
         roof["launches_per_step"] = nl / len(prof_times)
-        roof["work_per_launch"] = work / nl
     kernels = {k: {"launches": v[0], "ms_per_step": round(v[1] / len(prof_times), 4),
                    "share": round(v[1] / max(1e-9, sum(x[1] for x in prof.values())), 4)} for k, v in prof.items()}
 
@@ -484,9 +606,7 @@ def run_ours(args, rank, world, local_rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": spec.dtype, "data": "synthetic (seeded generator; tables, weights, dense, Zipf bags)",
-        "config": {"workload": desc, "invocations_per_step": n_inv, "global_batch": M * world,
-                   "lookups_per_step": nidx, "seq_len": None, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MiB write outside the events)"},
+        "config": config_of(desc, n_inv, M, nidx, world),
         "latency_fused_step": lat,
         "plain": {"invocations_per_s": round(plain_rate * world, 2),
                   "ms_per_step": round(sum(plain_times) / len(plain_times), 4),
@@ -499,7 +619,8 @@ def run_ours(args, rank, world, local_rank):
                     "K": int(t[3]), "bn": int(t[4]), "stages": int(t[5])} for t in tuning],
         "kernels": kernels,
         "roofline": roof,
-        "rooflines_by_kernel": {k: {x: v[x] for x in ("bound", "achieved", "peak", "unit", "frac")}
+        "rooflines_by_kernel": {k: {x: v[x] for x in ("bound", "achieved", "peak", "unit", "frac")
+                                    + (("effective_GBs", "traffic") if k == "gather" else ())}
                                 for k, v in rooflines.items()},
         "e2e": {"value": round(world * n_inv * e2e_steps / e2e_s, 2), "unit": "invocations/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "matches_device_path": e2e_match,
@@ -570,6 +691,60 @@ def make_trace(specs, n, rate, per_fn_invs, seed, burst=False, fns=None, arrival
     return reqs, out, pool_invs
 
 
+SERVE_KEYS = ("invocations_per_s", "p50_ms", "p99_ms", "warm_p50_ms", "warm_p99_ms", "cold_p50_ms", "cold_p99_ms",
+              "completed", "batches", "prepares", "evictions", "cold_requests", "max_inflight_batches", "wall_s")
+
+
+def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), **kw):
+    """Replay one trace once per mode on a fresh pool: cold (every function prepared at
+    its first request: setup inside the latencies) or warm (every function resident
+    and ready first).  mode = (name, max_batch_invocations): 0 = continuous batching,
+    1 = one invocation per launch (the plain form).  Returns ({mode: stats}, {mode:
+    outputs})."""
+    import paper_2404_14691_b300 as sage
+    fkw = [workload.prepare_kwargs(s) for s in specs]
+    res, outs = {}, {}
+    for mode, mbi in modes:
+        pool = sage.Pool(device=0)
+        held = []
+        if warm:
+            held = [pool.prepare(**workload.prepare_kwargs(s)) for s in specs]
+            for h in held:
+                h.wait()
+        r, st = sage.serve(pool, fkw, reqs, max_batch_invocations=mbi, lanes_per_fn=kw.pop("lanes_per_fn", 2),
+                           **kw)
+        outs[mode] = out.clone()
+        for h in held:
+            h.release()
+        pool.destroy()
+        res[mode] = {k: (round(st[k], 3) if isinstance(st[k], float) else st[k]) for k in SERVE_KEYS}
+        res[mode]["mean_batch_invocations"] = round(float(np.mean([x["batch_invocations"] for x in r])), 2)
+    return res, outs
+
+
+def serving_summary(args):
+    """The serving workload's headline numbers: 2,000 requests, Poisson 200/s over the 4
+    bf16 functions, continuous batching vs one invocation per launch, from a cold start
+    (p50/p99 latency including setup) and with every function resident (warm)."""
+    import torch
+    specs = workload.spec_c4_functions()
+    reqs, out, keep = make_trace(specs, args.requests, 200.0, 8,
+                                 seed=workload.sub_seed("serve", "trace") % (1 << 63))
+    cold, co = serve_modes(specs, reqs, out, warm=False)
+    warm, wo = serve_modes(specs, reqs, out, warm=True)
+    same = all(bool(torch.equal(co["served"], x)) for x in (co["plain"], wo["served"], wo["plain"]))
+    total_ro = sum(s.table_bytes() for s in specs)
+    return {"workload": "serving: %d requests, Poisson 200/s over 4 bf16 functions (8x1Mx64, 26x1Mx128, "
+                        "26x4Mx128, 52x2Mx64; %.1f GB read-only), B~round(LogNormal(ln256,1)), L~U[1,100]; "
+                        "requests from pinned host buffers" % (args.requests, total_ro / 1e9),
+            "cold_start": cold, "warm": warm, "outputs_identical": same,
+            "served_beats_plain": {
+                "cold_p99": cold["served"]["p99_ms"] < cold["plain"]["p99_ms"],
+                "warm_p99": warm["served"]["p99_ms"] < warm["plain"]["p99_ms"],
+                "cold_invocations_per_s": cold["served"]["invocations_per_s"] >= cold["plain"]["invocations_per_s"],
+                "warm_invocations_per_s": warm["served"]["invocations_per_s"] >= warm["plain"]["invocations_per_s"]}}
+
+
 def run_serve(args):
     """The serving workload: 2000 requests, Poisson arrivals at 200/s over 4 BF16 functions (cold start),
     continuous batching vs one invocation per launch; then a warm saturation burst."""
@@ -582,17 +757,8 @@ def run_serve(args):
     link = h2d_link_gbs(torch)
     reqs, out, keep = make_trace(specs, n, 200.0, 8, seed=workload.sub_seed("serve", "trace") % (1 << 63))
     fkw = [workload.prepare_kwargs(s) for s in specs]
-    res = {}
     sampler.start()
-    outs = {}
-    for mode, mbi in (("served", 0), ("plain", 1)):
-        pool = sage.Pool(device=0)
-        r, st = sage.serve(pool, fkw, reqs, max_batch_invocations=mbi, lanes_per_fn=2)
-        outs[mode] = out.clone()
-        pstats = pool.stats()
-        pool.destroy()
-        res[mode] = {k: (round(v, 3) if isinstance(v, float) else v) for k, v in st.items()}
-        res[mode]["mean_batch_invocations"] = round(float(np.mean([x["batch_invocations"] for x in r])), 2)
+    res, outs = serve_modes(specs, reqs, out, warm=False)
     same = bool(torch.equal(outs["served"], outs["plain"]))
     # warm saturation: every function resident (held by this process), all requests at t = 0
     burst, bout, keep2 = make_trace(specs, n, 200.0, 8, seed=workload.sub_seed("serve", "trace") % (1 << 63),
@@ -918,46 +1084,42 @@ def run_share(args):
 
 def cpu_baseline(spec, invs, budget_s):
     threads = os.cpu_count() or 1
-    rate, done, samples, el = oracle_rate(spec, invs, budget_s, threads)
+    rate, done, samples, el = oracle_timing(spec, invs, budget_s, threads)
     return {"value": round(rate, 4), "unit": "invocations/s", "cores": threads, "kind": "oracle",
-            "sample": "%d of the %d invocations of one step (%d samples) in %.1f s, fp64 C oracle, %d threads"
+            "sample": "%d whole invocations of the step's %d (%d samples) in %.1f s, fp64 C oracle, %d threads; "
+                      "invocations/s = samples/s / the step's mean samples per invocation"
                       % (done, len(invs), samples, el, threads)}
 
 
 def run_reference(args, rank, world):
-    """The CPU oracle timed as it stands on this workload (rank 0 only)."""
+    """The CPU oracle timed as it stands on this workload (rank 0 only): each step is a
+    bounded sample of whole invocations, continuing through the step's invocations."""
     spec, invs, desc = make_workload(args.workload, 0)
     threads = os.cpu_count() or 1
-    import oracle
-    w = workload.weights_arrays(spec)
-    src = lambda t, r: workload.table_rows(spec, t, r)
-    # bounded sample per step: whole invocations, cycling through the step's invocations
     budget_per_step = min(10.0, 150.0 / max(1, args.steps + args.warmup))
     k = 0
-    done = 0
+    done = samples = 0
     t_total = 0.0
     for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        n = 0
-        while True:
-            oracle.forward(spec, w, invs[k % len(invs)], row_source=src, n_threads=threads, want_pooled=False)
-            k += 1
-            n += 1
-            if time.perf_counter() - t0 > budget_per_step:
-                break
-        el = time.perf_counter() - t0
+        r, n, smp, el = oracle_timing(spec, invs, budget_per_step, threads, start=k)
+        k += n
         if s >= args.warmup:
             done += n
+            samples += smp
             t_total += el
-    rate = done / t_total
+    mean_batch = float(np.mean([v["batch"] for v in invs]))
+    rate = samples / t_total / mean_batch
+    M = int(sum(v["batch"] for v in invs))
     line = {"impl": "reference", "metric": METRIC, "value": round(rate, 4), "unit": "invocations/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_total / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "invocations_per_step": len(invs)},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator; tables, weights, dense, Zipf bags)",
+            "config": config_of(desc, len(invs), M, n_indices(invs), world),
             "cpu_baseline": {"value": round(rate, 4), "unit": "invocations/s", "cores": threads, "kind": "oracle",
-                             "sample": "each step: whole invocations of the workload for ~%.2f s (%d in total), "
-                                       "fp64 C oracle, %d threads" % (budget_per_step, done, threads)},
+                             "sample": "each step: whole invocations of the workload for ~%.2f s (%d in total, %d "
+                                       "samples), fp64 C oracle, %d threads; invocations/s = samples/s / the "
+                                       "workload's mean samples per invocation"
+                                       % (budget_per_step, done, samples, threads)},
             "e2e": {"value": round(rate, 4), "unit": "invocations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     return line
@@ -969,7 +1131,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c3")
     ap.add_argument("--cpu-budget-s", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -979,6 +1141,8 @@ def main():
     ap.add_argument("--stress-functions", type=int, default=16)
     ap.add_argument("--stress-invocations", type=int, default=256)
     ap.add_argument("--share-reps", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the uniform control, fp32 batching and serving keys")
     ap.add_argument("--profile-only", action="store_true",
                     help="only warm-up + timed fused steps (for ncu launch lists); prints a short line")
     args = ap.parse_args()
@@ -1014,6 +1178,11 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     line, spec, invs = run_ours(args, rank, world, local_rank)
     if rank == 0:
+        if args.workload == "c3" and not args.profile_only and not args.no_extras and world == 1:
+            # the metric's other parts, on the same GPU after the headline steps
+            line["uniform_control"] = uniform_control(args, local_rank)
+            line["batching_fp32"] = fused_batch_summary(args, "c2", local_rank, plain=True)
+            line["serving"] = serving_summary(args)
         if not args.no_cpu_baseline and not args.profile_only:
             line["cpu_baseline"] = cpu_baseline(spec, invs, args.cpu_budget_s)
         print(json.dumps(line), flush=True)

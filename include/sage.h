@@ -274,6 +274,22 @@ sage_status sage_invoke_batch_host_async(sage_fn fn, const sage_host_invocation*
  * skipped) or SAGE_ERR_DEVICE (a kernel's bounded wait ran out). */
 sage_status sage_fn_check(sage_fn fn);
 
+/* Test read-back: copy one activation buffer of the most recent batch that ran on
+ * this function's key (any handle, any sage_invoke* call) to host memory `dst`,
+ * after waiting for that batch.  which = 0: the concat buffer [M, T*dim +
+ * bot_dims[n_bot-1]] (the gather's pooled columns, then the bottom MLP's output);
+ * which = 1 + l: the output of top hidden layer l [M, top_dims[l]], l < n_top - 1,
+ * when it is written (SAGE_ERR_INVALID for the last hidden layer when the sigmoid
+ * head runs in its epilogue).  Rows are the batch's samples in invocation order.
+ * plane 0: the values as stored (fp32; bf16 for SAGE_BF16 functions; for fp32
+ * functions whose hidden layers run on the tensor cores, the tf32-rounded "hi"
+ * part), plane 1: the fp32 residual "lo" of such functions (value = hi + lo
+ * exactly), else SAGE_ERR_INVALID.  bytes must be M * width * element size.
+ * *rows_out (may be NULL) receives M; with dst NULL nothing is copied.  A later
+ * batch may reuse the workspace: call it before the next batch.  The paper has no
+ * counterpart (it lets tests compare intermediate results with the oracle). */
+sage_status sage_fn_debug_copy(sage_fn fn, int which, int plane, void* dst, size_t bytes, int* rows_out);
+
 /* Drop a reference (the handle is invalid afterwards).  When the last reference
  * of a key is dropped, the pool waits for the key's in-flight work, frees its
  * device copy and workspace and returns the budget -- or, with host_cache_bytes,

@@ -193,6 +193,19 @@ class Function:
         check(lib().sage_invoke_batch_host_async(self.handle, arr, len(arr), _stream_handle(stream)),
               "sage_invoke_batch_host_async")
 
+    def debug_copy(self, which: int, width: int, bf16: bool, plane: int = 0):
+        """Copy an activation buffer of the most recent batch (sage_fn_debug_copy):
+        which 0 = concat [M, width = T*dim + bot], 1 + l = top hidden layer l [M,
+        width = top_dims[l]].  Returns a numpy array [M, width]: float32, or the
+        uint16 bit patterns of bf16 values when bf16 is true."""
+        import numpy as np
+        rows = ctypes.c_int(0)
+        check(lib().sage_fn_debug_copy(self.handle, which, plane, None, 0, ctypes.byref(rows)), "sage_fn_debug_copy")
+        out = np.empty((rows.value, int(width)), dtype=np.uint16 if bf16 else np.float32)
+        check(lib().sage_fn_debug_copy(self.handle, which, plane, out.ctypes.data, out.nbytes, None),
+              "sage_fn_debug_copy")
+        return out
+
     def check_errors(self) -> None:
         """Raise SageError if a kernel saw an out-of-range row or a timed-out wait."""
         check(lib().sage_fn_check(self.handle), "sage_fn_check")

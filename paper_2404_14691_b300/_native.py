@@ -115,6 +115,7 @@ SIGNATURES = [
     ("sage_invoke_batch_host", _i, [_vp, ctypes.POINTER(HostInvocation), _i, _vp]),
     ("sage_invoke_batch_host_async", _i, [_vp, ctypes.POINTER(HostInvocation), _i, _vp]),
     ("sage_fn_check", _i, [_vp]),
+    ("sage_fn_debug_copy", _i, [_vp, _i, _i, _vp, _sz, ctypes.POINTER(_i)]),
     ("sage_release", _i, [_vp]),
     ("sage_pool_destroy", _i, [_vp]),
     ("sage_pool_stats", _i, [_vp, ctypes.POINTER(PoolStats)]),

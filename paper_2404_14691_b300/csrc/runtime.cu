@@ -204,6 +204,9 @@ struct Slot {
   // update `exec` (same kernels, new parameters), which is launched in one call
   cudaStream_t capture = nullptr;
   cudaGraphExec_t exec = nullptr;
+  // top hidden layers whose outputs the last launch chain wrote (the last hidden
+  // layer is not written when the head runs in its epilogue)
+  int top_written = 0;
 };
 
 }  // namespace
@@ -267,6 +270,7 @@ struct Entry {
   std::vector<Slot> slots;
   int next_slot = 0;
   int max_batch = 4096;
+  int last_slot = -1, last_M = 0;  // the slot and rows of the most recent batch
 
   int concat_dim() const { return T * dim + bot.back(); }
   size_t elem() const { return dtype == SAGE_BF16 ? 2 : 4; }
@@ -940,6 +944,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   const char* x = s.concat;
   int ldx = cd;
   const Layer& H = e->layers[nb + nt - 1];
+  s.top_written = 0;
   for (int l = 0; l + 1 < nt; ++l) {
     const Layer& L = e->layers[nb + l];
     char* y = s.top[l];
@@ -984,6 +989,7 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
       SAGE_CK(launch_f32_layer(M, L.out, L.in, reinterpret_cast<const float*>(x), ldx,
                                static_cast<const float*>(L.W), L.b, 1, reinterpret_cast<float*>(y), L.out,
                                e->d_err, stream));
+    s.top_written = l + 1;
     x = y;
     ldx = L.out;
   }
@@ -1017,6 +1023,8 @@ sage_status acquire_slot(Entry* e, int M, cudaStream_t stream, Slot** out, int w
     sage_status st = build_slot(e, s, cap, stream);
     if (st != SAGE_OK) return st;
   }
+  e->last_slot = static_cast<int>(&s - e->slots.data());
+  e->last_M = M;
   *out = &s;
   return SAGE_OK;
 }
@@ -1765,6 +1773,39 @@ sage_status sage_fn_check(sage_fn f) {
   }
   if (w & kErrTimeout) return fail(SAGE_ERR_DEVICE, "a kernel's bounded wait ran out");
   if (w & kErrBounds) return fail(SAGE_ERR_BOUNDS, "a bag row index was outside its table");
+  return SAGE_OK;
+}
+
+sage_status sage_fn_debug_copy(sage_fn f, int which, int plane, void* dst, size_t bytes, int* rows_out) {
+  if (!valid_fn(f)) return fail(SAGE_ERR_INVALID, "invalid function handle");
+  Entry* e = f->e;
+  std::lock_guard<std::mutex> g(e->imu);
+  if (e->last_slot < 0) return fail(SAGE_ERR_INVALID, "no batch has run on this function");
+  const int M = e->last_M;
+  if (rows_out) *rows_out = M;
+  if (!dst) return SAGE_OK;
+  Slot& s = e->slots[e->last_slot];
+  const int nt = static_cast<int>(e->top.size());
+  const char* buf = nullptr;
+  int width = 0;
+  if (which == 0) {
+    buf = s.concat;
+    width = e->concat_dim();
+  } else if (which >= 1 && which < nt) {
+    if (which > s.top_written)
+      return fail(SAGE_ERR_INVALID, "top hidden layer %d is not written (the head runs in its epilogue)", which - 1);
+    buf = s.top[which - 1];
+    width = e->top[which - 1];
+  } else {
+    return fail(SAGE_ERR_INVALID, "buffer %d does not exist", which);
+  }
+  if (plane < 0 || plane >= static_cast<int>(planes(e))) return fail(SAGE_ERR_INVALID, "plane %d does not exist", plane);
+  const size_t need = static_cast<size_t>(M) * width * e->elem();
+  if (bytes != need) return fail(SAGE_ERR_INVALID, "bytes %zu != %zu", bytes, need);
+  if (plane == 1) buf += static_cast<size_t>(s.cap) * width * e->elem();
+  SAGE_CK(cudaSetDevice(e->pool->device));
+  if (s.used) SAGE_CK(cudaEventSynchronize(s.done));
+  SAGE_CK(cudaMemcpy(dst, buf, need, cudaMemcpyDeviceToHost));
   return SAGE_OK;
 }
 

@@ -79,3 +79,54 @@ def oracle_rows(spec, weights, inv, rows, n_threads=8):
         mag[i:j + 1] = res["out_mag"]
         i = j + 1
     return out, mag
+
+
+# ---------------------------------------------------------------- element-wise checks of intermediate buffers
+
+def check_rounded_bag_sums(got, ref, mag, out_bits: int) -> dict:
+    """Pooled bag sums against the oracle, with the bound that the arithmetic fixes.
+
+    The kernels add a bag's rows in fp32 (any fixed order) and round the sum once to
+    the output type: for bags of at most 128 rows the fp32 sum errs by at most
+    127 * 2^-24 * mag <= 2^-17 * mag (mag = the sum of |terms|), and rounding to
+    nearest with `out_bits` significand bits (bf16: 8, fp32: 24) adds at most
+    2^-out_bits * |sum|.  So |got - ref| <= 2^-out_bits * |ref| + 2^-16 * mag.  For
+    long bf16 bags this is far stricter than 2e-2 * mag, which most elements of a
+    100-row bag with one row dropped would still meet."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    mag = np.asarray(mag, dtype=np.float64)
+    bound = 2.0 ** -out_bits * np.abs(ref) + 2.0 ** -16 * mag
+    err = np.abs(got - ref)
+    ok = err <= bound
+    return {"ok": bool(ok.all()), "n": int(ok.size), "n_bad": int((~ok).sum()),
+            "max_err_over_bound": float((err / np.where(bound > 0, bound, 1)).max()) if err.size else 0.0}
+
+
+def oracle_pooled(spec, inv):
+    """Oracle pooled bags [B, T*D] and magnitudes of one invocation (only referenced rows read)."""
+    B = inv["batch"]
+    tabs, idx, off = oracle.compact_tables(spec, inv, 0, B, lambda t, r: workload.table_rows(spec, t, r))
+    return oracle.bag_sum(tabs, idx, off, B)
+
+
+def oracle_bottom(spec, weights, dense):
+    """Oracle bottom MLP output and magnitudes for dense rows [n, n_dense]."""
+    h = np.asarray(dense, dtype=np.float64)
+    m = np.abs(h)
+    for l in range(len(spec.bot_dims)):
+        W, b = weights[l]
+        h, m = oracle.linear(h, W, b, relu=True, xmag=m)
+    return h, m
+
+
+def oracle_top0(spec, weights, concat, concat_mag, n_threads=8):
+    """Oracle first top hidden layer ReLU(c V0^T + e0) and magnitudes, rows split over threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    W, b = weights[len(spec.bot_dims)]
+    n = concat.shape[0]
+    cuts = np.linspace(0, n, n_threads + 1).astype(int)
+    with ThreadPoolExecutor(n_threads) as ex:
+        parts = list(ex.map(lambda k: oracle.linear(concat[cuts[k]:cuts[k + 1]], W, b, relu=True,
+                                                    xmag=concat_mag[cuts[k]:cuts[k + 1]]), range(n_threads)))
+    return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])

@@ -39,17 +39,25 @@ def test_committed_traffic_entries_name_existing_sources():
 
 
 def test_roofline_of_each_kernel_kind():
-    """achieved = work per launch / mean launch time, against the kind's bound."""
+    """Gather: achieved = DRAM bytes per launch (from an ncu capture) / mean launch time,
+    against the HBM copy rate, beside the effective (algorithmic) rate; GEMMs:
+    algorithmic flops / mean launch time against the burst tensor peak."""
     peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1500.0, "sm_max_mhz": 2000.0}
-    # 4 launches in 2 ms in all, 8e9 bytes of work in all: 2e9 B per 0.5 ms = 4000 GB/s
-    g = bench.roofline_of("gather", 4, 2.0, 8e9, peaks, "test")
-    assert g["bound"] == "hbm" and g["unit"] == "GB/s" and abs(g["achieved"] - 4000.0) < 1e-6
-    assert abs(g["frac"] - 4000.0 / 6000.0) < 1e-4
-    # bf16 GEMMs against the sustained bf16 peak: 3e12 flop in 2 ms over 2 launches = 1500 TF/s
+    # 4 launches in 2 ms in all, 8e9 algorithmic bytes in all: 2e9 B per 0.5 ms = 4000 GB/s effective;
+    # 1e9 DRAM bytes per launch: 2000 GB/s of DRAM = 1/3 of the copy rate
+    g = bench.roofline_of("gather", 4, 2.0, 8e9, peaks, "test", traffic=1e9)
+    assert g["bound"] == "hbm" and g["unit"] == "GB/s"
+    assert abs(g["effective_GBs"] - 4000.0) < 1e-6 and abs(g["effective_over_hbm"] - 4000.0 / 6000.0) < 1e-4
+    assert abs(g["achieved"] - 2000.0) < 1e-6 and abs(g["frac"] - 2000.0 / 6000.0) < 1e-4
+    assert g["traffic"] == 1e9
+    # without a capture of the current source there is no DRAM figure, only the effective one
+    g0 = bench.roofline_of("gather", 4, 2.0, 8e9, peaks, "test")
+    assert g0["achieved"] is None and g0["frac"] is None and abs(g0["effective_GBs"] - 4000.0) < 1e-6
+    # bf16 GEMMs against the burst bf16 peak: 3e12 flop in 2 ms over 2 launches = 1500 TF/s
     t = bench.roofline_of("gemm_tc", 2, 2.0, 3e12, peaks, "test")
-    assert t["bound"] == "tensor" and abs(t["achieved"] - 1500.0) < 1e-6 and abs(t["frac"] - 1.0) < 1e-4
-    # fp32 as three tf32 products (and the fused bottom kernel): tf32 = bf16 x 1.1 / 2.25, / 3
-    ceiling = 1500.0 * 1.1 / 2.25 / 3.0
+    assert t["bound"] == "tensor" and abs(t["achieved"] - 1500.0) < 1e-6 and abs(t["frac"] - 1500.0 / 1800.0) < 1e-4
+    # fp32 as three tf32 products (and the fused bottom kernel): tf32 = bf16 burst x 1.1 / 2.25, / 3
+    ceiling = 1800.0 * 1.1 / 2.25 / 3.0
     for kind in ("gemm_tf32x3", "bottom01"):
         f = bench.roofline_of(kind, 1, 1.0, 1e11, peaks, "test")   # 100 TF/s
         assert f["bound"] == "tensor" and abs(f["peak"] - round(ceiling, 1)) < 1e-6
@@ -57,3 +65,23 @@ def test_roofline_of_each_kernel_kind():
     # anything else: the FP32 pipes at the maximum SM clock
     a = bench.roofline_of("bottom0", 1, 1.0, 1e10, peaks, "test")
     assert a["bound"] == "alu" and abs(a["peak"] - 148 * 128 * 2 * 2000e6 / 1e12) < 0.01
+
+
+def test_oracle_timing_normalises_by_the_mean_invocation(monkeypatch):
+    """Both oracle legs (cpu_baseline and the reference arm) report samples/s divided by
+    the workload's mean samples per invocation, whichever invocations they timed."""
+    import time as _t
+    import oracle
+    calls = []
+
+    def fake_forward(spec, w, v, **kw):
+        calls.append(v["batch"])
+        _t.sleep(0.001 * v["batch"])        # 1 ms per sample
+
+    monkeypatch.setattr(oracle, "forward", fake_forward)
+    monkeypatch.setattr(bench.workload, "weights_arrays", lambda spec: None)
+    invs = [{"batch": 10}, {"batch": 30}]          # mean 20 samples
+    rate, done, samples, el = bench.oracle_timing(None, invs, 0.15, 1, start=1)
+    assert calls[0] == 30 and done == len(calls) and samples == sum(calls)
+    # ~1000 samples/s / 20 samples per invocation = ~50 invocations/s
+    assert 30.0 < rate < 55.0

@@ -375,6 +375,10 @@ def test_multistage_exit_restages_from_the_host_cache():
         f2.invoke(*d2.args())
         torch.cuda.synchronize()
         assert torch.equal(d1.out, d2.out)
+        # and both against the oracle: the re-staged data is the function's data (Sec. 6.3)
+        w = workload.weights_arrays(spec)
+        _check_inv(spec, w, d1, RTOL["bf16"])
+        _check_inv(spec, w, d2, RTOL["bf16"])
         st = p.stats()
         assert st["host_cache_hits"] == 1 and st["host_cache_entries"] == 0
         f2.release()
