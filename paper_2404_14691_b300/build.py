@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libsage.so")
-SOURCES = ["runtime.cu", "gather.cu", "mlp_simt.cu", "gemm_tc.cu", "gemm_tf32.cu", "bottom_fused.cu", "noalloc.cu",
+SOURCES = ["runtime.cu", "gather.cu", "gather_gemm.cu", "mlp_simt.cu", "gemm_tc.cu", "gemm_tf32.cu", "bottom_fused.cu", "noalloc.cu",
            "serve.cu", "tune.cu", "share.cu", "partition.cu"]
 HEADERS = ["common.cuh", "kernels.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

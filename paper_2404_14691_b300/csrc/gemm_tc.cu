@@ -500,6 +500,11 @@ int gemm_candidates(int kind, GemmCfg* out, int max) {
     n = tf32_presplit_candidates(out, max);
   } else if (kind == kBottom01) {
     n = bottom01_candidates(out, max);
+  } else if (kind == kGatherTop0) {
+    // the gather and the first top layer in one kernel, or separate kernels
+    const GemmCfg c[2] = {{256, 2}, {1, 1}};
+    for (const GemmCfg& x : c)
+      if (n < max) out[n++] = x;
   } else {
     n = tf32_candidates(out, max);
   }

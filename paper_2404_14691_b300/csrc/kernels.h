@@ -65,7 +65,7 @@ struct GemmCfg {
   int bn;
   int stages;
 };
-enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2, kGemmTf32Pre = 3, kBottom01 = 4 };
+enum : int { kGemmBf16 = 1, kGemmTf32x3 = 2, kGemmTf32Pre = 3, kBottom01 = 4, kGatherTop0 = 5 };
 int gemm_candidates(int kind, GemmCfg* out, int max);
 int tf32_candidates(GemmCfg* out, int max);
 int tf32_presplit_candidates(GemmCfg* out, int max);
@@ -119,6 +119,18 @@ cudaError_t launch_bottom01_f32(const InvTable& tab, int K0, int N0, const float
                                 int* err, cudaStream_t s, GemmCfg cfg, const float* w2h = nullptr,
                                 const float* w2l = nullptr, const float* b2 = nullptr, int N2 = 0,
                                 int* layers = nullptr);
+// The gather and the first top layer of a pre-split fp32 function in one kernel:
+// y = ReLU([pooled, bottom] W0^T + b0) as hi/lo planes, the pooled columns summed
+// straight into the GEMM's shared-memory A tiles (never written), the bottom
+// output's columns read from x (hi/lo planes of the concat buffer, row stride ldx,
+// written before the launch).  Tables of 64 fp32 columns; N0 = 256 or 512; K0 =
+// T * 64 + the bottom output's width (a multiple of 32).  Same bits as
+// launch_gather followed by launch_linear_f32_tc_presplit.
+bool gather_top0_fusable(int dtype, int dim, int T, int n_bot_out, int N0, bool presplit);
+cudaError_t launch_gather_top0_f32(const GatherArgs& a, const InvTable& tab, int N0, int K0, const float* xh,
+                                   const float* xl, int ldx, const float* wh, const float* wl, const float* b0,
+                                   float* yh, float* yl, int ldy, int* err, cudaStream_t s);
+void preload_gather_top0_kernels();
 // hi[i] = tf32(src[i]) (round to nearest), lo[i] = src[i] - hi[i].
 cudaError_t launch_split_planes(const float* src, float* hi, float* lo, size_t n, cudaStream_t s);
 // fp32 layer on the tensor cores: three tf32 products of the hi/lo split of x and W.

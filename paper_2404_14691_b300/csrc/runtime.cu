@@ -207,6 +207,8 @@ struct Slot {
   // top hidden layers whose outputs the last launch chain wrote (the last hidden
   // layer is not written when the head runs in its epilogue)
   int top_written = 0;
+  // false when the gather ran fused with the first top layer (no pooled columns written)
+  bool pooled_written = true;
 };
 
 }  // namespace
@@ -505,10 +507,11 @@ enum ProfKind {
   kProfHead,
   kProfGemmTf32,
   kProfBottom01,
+  kProfGatherTop0,
   kProfKinds
 };
-const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32",    "gemm_tc", "gather",
-                                            "head",    "gemm_tf32x3", "bottom01"};
+const char* const kProfNames[kProfKinds] = {"bottom0", "gemm_f32",    "gemm_tc",  "gather",
+                                            "head",    "gemm_tf32x3", "bottom01", "gather_top0"};
 
 struct ProfRec {
   int kind;
@@ -561,6 +564,7 @@ double load_kernels_once() {
     preload_tc_kernels();
     preload_tf32_kernels();
     preload_bottom01_kernels();
+    preload_gather_top0_kernels();
     g_load_ms = ms_since(t0);
     spent = g_load_ms;
   });
@@ -854,7 +858,17 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
   // (while kernel timing is on, the branch is serialised so that each kernel's
   // events measure it alone; on a confined stream -- an SM partition -- it stays
   // on that stream so that every kernel runs on the partition's SMs)
-  const bool overlap = !g_prof_on.load(std::memory_order_relaxed) && !confined;
+  // the gather and the first top layer as one kernel (pre-split fp32 functions with
+  // 64-column tables), when tuning kind 5 asks for it ((256, 2); untuned or (1, 1):
+  // separate kernels, which measured faster on the batching workload -- the fused
+  // kernel's one CTA per SM keeps half the gather's loads in flight).  It reads the
+  // bottom MLP's output, so the bottom MLP then runs first, on the launch stream.
+  bool fuse_g0 = false;
+  if (ps2 && nt >= 2 && gather_top0_fusable(e->dtype, e->dim, e->T, e->bot.back(), e->top[0], true)) {
+    const GemmCfg c = tuned_gemm(kGatherTop0, M, e->top[0], cd);
+    fuse_g0 = c.bn == 256;
+  }
+  const bool overlap = !g_prof_on.load(std::memory_order_relaxed) && !confined && !fuse_g0;
   SAGE_CK(cudaEventRecord(s.fork, stream));
   SAGE_CK(cudaStreamWaitEvent(s.branch, s.fork, 0));
   const cudaStream_t main_stream = stream;
@@ -935,17 +949,32 @@ sage_status launch_chain(Entry* e, Slot& s, const InvTable& tab, cudaStream_t st
     double lookups = 0;
     for (int i = 0; i < tab.n; ++i) lookups += static_cast<double>(tab.d[i].nidx);
     const double row = static_cast<double>(e->dim) * es;
-    ProfScope ps(stream, kProfGather, lookups * (row + 4.0) + static_cast<double>(e->T) * M * (8.0 + row));
-    SAGE_CK(launch_gather(a, tab, stream));
+    const double bytes = lookups * (row + 4.0) + static_cast<double>(e->T) * M * (8.0 + row);
+    if (!fuse_g0) {
+      ProfScope ps(stream, kProfGather, bytes);
+      SAGE_CK(launch_gather(a, tab, stream));
+    } else {
+      // the bottom MLP ran on this stream already; the pooled columns stay on chip
+      // (the work recorded is the gather's bytes without the pooled write)
+      SAGE_CK(cudaStreamWaitEvent(stream, s.join, 0));
+      const Layer& L = e->layers[nb];
+      ProfScope ps(stream, kProfGatherTop0, bytes - static_cast<double>(e->T) * M * row);
+      SAGE_CK(launch_gather_top0_f32(a, tab, L.out, L.in, reinterpret_cast<const float*>(s.concat),
+                                     lo_of(s.concat, cd), cd, e->wplanes[nb].first, e->wplanes[nb].second, L.b,
+                                     reinterpret_cast<float*>(s.top[0]), lo_of(s.top[0], L.out), L.out, e->d_err,
+                                     stream));
+    }
   }
   // join: the top MLP needs both halves of the concat buffer
   SAGE_CK(cudaStreamWaitEvent(stream, s.join, 0));
-  // top MLP hidden layers
-  const char* x = s.concat;
-  int ldx = cd;
+  // top MLP hidden layers (the first one is done when the gather ran fused with it)
+  const int l0 = fuse_g0 ? 1 : 0;
+  const char* x = fuse_g0 ? s.top[0] : s.concat;
+  int ldx = fuse_g0 ? e->top[0] : cd;
   const Layer& H = e->layers[nb + nt - 1];
-  s.top_written = 0;
-  for (int l = 0; l + 1 < nt; ++l) {
+  s.top_written = l0;
+  s.pooled_written = !fuse_g0;
+  for (int l = l0; l + 1 < nt; ++l) {
     const Layer& L = e->layers[nb + l];
     char* y = s.top[l];
     if (l + 2 == nt && s.hcnt) {
@@ -1789,6 +1818,9 @@ sage_status sage_fn_debug_copy(sage_fn f, int which, int plane, void* dst, size_
   const char* buf = nullptr;
   int width = 0;
   if (which == 0) {
+    if (!s.pooled_written)
+      return fail(SAGE_ERR_INVALID, "the pooled columns are not written (the gather ran fused with the first top "
+                                    "layer; tuning kind 5 set to (1, 1) keeps them)");
     buf = s.concat;
     width = e->concat_dim();
   } else if (which >= 1 && which < nt) {

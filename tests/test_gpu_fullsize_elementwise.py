@@ -27,7 +27,10 @@ pytestmark = pytest.mark.gpu
 sage = pytest.importorskip("paper_2404_14691_b300")
 
 
-def _fused_batch(name):
+def _fused_batch(name, gather_top0=None):
+    """The workload's fused batch as the benchmark runs it; gather_top0 True / False
+    pins the gather + first-top-layer fusion on / off (fp32 functions), None leaves
+    the default."""
     import bench
     import torch
     spec, invs, _ = bench.make_workload(name)
@@ -35,6 +38,8 @@ def _fused_batch(name):
     pool = sage.Pool(device=0, graphs=True)
     fn = prepare(pool, spec, max_batch=max(4096, M), workspace_slots=2)
     fn.autotune(M)
+    if gather_top0 is not None:
+        sage.tuning_set(5, M, spec.top_dims[0], spec.concat_dim, 256 if gather_top0 else 1, 2 if gather_top0 else 1)
     dinv = [DevInvocation(v) for v in invs]
     fn.invoke_batch([d.args() + (int(v["indices"].size),) for v, d in zip(invs, dinv)])
     torch.cuda.synchronize()
@@ -81,9 +86,10 @@ def _check_top0(spec, w, fn, M, row0, B, ref_concat, ref_mag, rtol, report):
 
 
 def test_batching_fp32_64_invocations_every_element():
-    """8 x 100,000 x 64 fp32, 64 invocations (~16k samples): every pooled and bottom
-    column of every invocation, and the first top hidden layer of every row."""
-    pool, fn, spec, invs, dinv, M = _fused_batch("c2")
+    """8 x 100,000 x 64 fp32, 64 invocations (~16k samples), the gather as its own
+    kernel: every pooled and bottom column of every invocation, and the first top
+    hidden layer of every row."""
+    pool, fn, spec, invs, dinv, M = _fused_batch("c2", gather_top0=False)
     try:
         w = workload.weights_arrays(spec)
         concat = _read(fn, spec, 0, spec.concat_dim)
@@ -102,6 +108,42 @@ def test_batching_fp32_64_invocations_every_element():
     finally:
         fn.release()
         pool.destroy()
+
+
+def test_batching_fp32_gather_fused_with_top0_every_element():
+    """The same batch with the gather fused into the first top layer (the pooled
+    columns never leave the chip): the first top hidden layer of every row against
+    the oracle, bitwise equal to the unfused chain's, and the outputs identical."""
+    import torch
+    pool, fn, spec, invs, dinv, M = _fused_batch("c2", gather_top0=True)
+    try:
+        w = workload.weights_arrays(spec)
+        hi = fn.debug_copy(1, spec.top_dims[0], bf16=False, plane=0)
+        report = {}
+        refs, mags = [], []
+        for v in invs:
+            pooled, pmag = oracle_pooled(spec, v)
+            bot, bmag = oracle_bottom(spec, w, v["dense"])
+            refs.append(np.concatenate([pooled, bot], axis=1))
+            mags.append(np.concatenate([pmag, bmag], axis=1))
+        _check_top0(spec, w, fn, M, 0, M, np.concatenate(refs), np.concatenate(mags), RTOL["f32"], report)
+        print("fp32 batching, gather fused with top layer 0, error vs fp64 oracle:", report)
+        fn.release()
+        pool.destroy()
+        pool2, fn2, _, _, dinv2, _ = _fused_batch("c2", gather_top0=False)
+        try:
+            assert np.array_equal(hi.view(np.uint32),
+                                  fn2.debug_copy(1, spec.top_dims[0], bf16=False, plane=0).view(np.uint32))
+            for a, b in zip(dinv, dinv2):
+                assert torch.equal(a.out, b.out)
+        finally:
+            fn2.release()
+            pool2.destroy()
+        fn = pool = None
+    finally:
+        if fn is not None:
+            fn.release()
+            pool.destroy()
 
 
 def test_precision_bf16_full_size_every_element_of_16_invocations():

@@ -30,16 +30,21 @@
 
 #define WL_GAMMA 0x9E3779B97F4A7C15ULL
 
-uint64_t wl_mix64(uint64_t z) {
+/* The loops below call these internal copies: the exported symbols can be
+ * interposed in a shared library, which would keep the compiler from inlining
+ * (and vectorising) them.  Same arithmetic, same values. */
+static inline uint64_t mix64_(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
     return z ^ (z >> 31);
 }
 
-uint64_t wl_draw(uint64_t seed, uint64_t e) { return wl_mix64(seed + (e + 1) * WL_GAMMA); }
+uint64_t wl_mix64(uint64_t z) { return mix64_(z); }
+
+uint64_t wl_draw(uint64_t seed, uint64_t e) { return mix64_(seed + (e + 1) * WL_GAMMA); }
 
 static inline float wl_value(uint64_t seed, uint64_t e, float step) {
-    int32_t k = (int32_t)(wl_draw(seed, e) >> 40) - 8388608;
+    int32_t k = (int32_t)(mix64_(seed + (e + 1) * WL_GAMMA) >> 40) - 8388608;
     return (float)k * step;
 }
 
