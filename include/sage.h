@@ -373,10 +373,10 @@ sage_status sage_tuning_load(const char* path);
  * loading, Sec. 5.1) and its requests queue until its data is ready.  Admission
  * is by device memory: a prepare that exceeds the pool budget evicts idle
  * resident functions (least recently used first) or waits.  Every function owns
- * lanes_per_fn streams, each with its own workspace slot; an idle lane takes ALL
- * queued requests of its function (up to the batch limits) as one fused batch,
- * so requests arriving while others run join the next batch, and lanes of
- * different functions overlap on the device.  An idle function keeps its data
+ * lanes_per_fn streams, each with its own workspace slot; the queued requests of
+ * a function are split evenly over its idle lanes and each lane runs its share
+ * (up to the batch limits) as one fused batch, so requests arriving while others
+ * run join the next batches, and lanes overlap on the device.  An idle function keeps its data
  * for linger_s (stage 1 of the multi-stage exit, Sec. 6.3), then is released.
  * Request buffers are host memory (pinned recommended): inputs are copied in and
  * outputs copied back inside each batch.  Latency = completion - arrival. */

@@ -6,10 +6,11 @@
 // requests queue.  Admission is by device memory: a prepare that does not fit the
 // pool budget evicts idle resident functions (least recently used first) and
 // otherwise waits.  Each function owns `lanes` streams, each with its own
-// workspace slot; whenever a lane is idle and requests are queued, all of them
-// (up to the batch limits) are fused into one launch chain on that lane -- so
-// requests that arrive while others run are batched as soon as a lane frees up,
-// and the lanes of different functions overlap on the device.  A resident
+// workspace slot; whenever lanes are idle and requests are queued, the queue is
+// split evenly over the idle lanes and each lane's share (up to the batch limits)
+// is fused into one launch chain -- so requests that arrive while others run are
+// batched as soon as a lane frees up, and the lanes of one function and of
+// different functions overlap on the device.  A resident
 // function with nothing queued or in flight keeps its data for `linger_s`
 // (the first stage of the paper's multi-stage exit, Sec. 6.3) and is then
 // released.  With sm_partition each function's lanes are streams of its own SM
@@ -199,13 +200,20 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
         S.ready = true;
         S.ready_at = now_s();
       }
+      // the queue is split evenly over the idle lanes (each then runs its share as one
+      // fused batch), so that queued requests run side by side instead of all in one
+      // lane's batch while the other lanes idle
+      int idle = 0;
+      for (const Lane& L : S.lanes) idle += L.busy ? 0 : 1;
       for (int li = 0; li < lanes && !S.queue.empty(); ++li) {
         Lane& L = S.lanes[li];
         if (L.busy) continue;
+        const int share = static_cast<int>((S.queue.size() + idle - 1) / idle);
+        --idle;
         hb.clear();
         L.reqs.clear();
         int64_t rows = 0;
-        while (!S.queue.empty() && static_cast<int>(hb.size()) < max_inv) {
+        while (!S.queue.empty() && static_cast<int>(hb.size()) < std::min(max_inv, share)) {
           const int id = S.queue.front();
           if (!hb.empty() && rows + reqs[id].inv.batch > max_rows) break;
           S.queue.pop_front();
