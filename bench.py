@@ -316,8 +316,16 @@ def fused_batch_summary(args, name, dev, plain=False):
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     step = lambda: fn.invoke_batch(args_all, stream=stream)
-    for _ in range(args.warmup):
+    # warm-up: the given steps, and at least half a second of them -- on the benchmark
+    # hosts a host thread that has been idle issues work several times slower for a
+    # while, which a batch this short (host-bound below ~0.3 ms) would measure
+    t0 = time.perf_counter()
+    k = 0
+    while k < args.warmup or time.perf_counter() - t0 < 0.5:
         step()
+        k += 1
+        if k % 16 == 0:
+            torch.cuda.synchronize()
     times = timed_steps(torch, stream, flush, step, args.steps)
     fn.check_errors()
     res = {"workload": desc, "invocations_per_step": len(invs), "samples_per_step": M,
