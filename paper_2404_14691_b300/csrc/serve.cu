@@ -279,9 +279,17 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
       }
     }
     if (!progressed) {
-      double wait = 20e-6;
-      if (next < order.size()) wait = std::min(wait, std::max(0.0, reqs[order[next]].arrival_s - now_s()));
-      if (wait > 0) std::this_thread::sleep_for(std::chrono::duration<double>(wait));
+      // nothing to do now.  With batches in flight, poll: a serving thread that sleeps
+      // between requests comes back slower on hosts whose idle cores clock down.  With
+      // requests queued only behind a function's staging, yield the core to the staging
+      // producers (short sleeps).  Idle: sleep until 1 ms before the next arrival, then poll.
+      bool queued = false;
+      for (const FnState& S : F) queued = queued || !S.queue.empty();
+      const double gap = next < order.size() ? reqs[order[next]].arrival_s - now_s() : 1e9;
+      if (inflight_total == 0 && queued)
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      else if (inflight_total == 0 && gap > 2e-3)
+        std::this_thread::sleep_for(std::chrono::duration<double>(gap - 1e-3));
     }
   }
   // drain and release
