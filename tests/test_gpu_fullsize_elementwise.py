@@ -74,6 +74,17 @@ def _check_invocation(spec, w, inv, concat_rows, rtol, bits, report):
     return np.concatenate([pooled, bot], axis=1), np.concatenate([pmag, bmag], axis=1)
 
 
+def _check_outputs(spec, w, inv, dinv, rtol, report, threads=16):
+    """Every final output (sigmoid) of one invocation against the oracle's, at the
+    componentwise bound and at the tolerance read literally."""
+    res = oracle.forward(spec, w, inv, row_source=lambda t, r: workload.table_rows(spec, t, r),
+                         n_threads=threads, want_pooled=False)
+    c = oracle.check_output(to_f64(dinv.out)[:inv["batch"]], res["out"], res["out_mag"], rtol)
+    assert c["ok"], c
+    report["out_max_rel"] = max(report.get("out_max_rel", 0.0), c["max_rel_err"])
+    report["outputs"] = report.get("outputs", 0) + c["n"]
+
+
 def _check_top0(spec, w, fn, M, row0, B, ref_concat, ref_mag, rtol, report):
     W0 = spec.top_dims[0]
     top0 = _read(fn, spec, 1, W0)
@@ -87,8 +98,8 @@ def _check_top0(spec, w, fn, M, row0, B, ref_concat, ref_mag, rtol, report):
 
 def test_batching_fp32_64_invocations_every_element():
     """8 x 100,000 x 64 fp32, 64 invocations (~16k samples), the gather as its own
-    kernel: every pooled and bottom column of every invocation, and the first top
-    hidden layer of every row."""
+    kernel: every pooled and bottom column of every invocation, the first top hidden
+    layer of every row, and every output."""
     pool, fn, spec, invs, dinv, M = _fused_batch("c2", gather_top0=False)
     try:
         w = workload.weights_arrays(spec)
@@ -104,6 +115,8 @@ def test_batching_fp32_64_invocations_every_element():
             mags.append(rm)
             row0 += B
         _check_top0(spec, w, fn, M, 0, M, np.concatenate(refs), np.concatenate(mags), RTOL["f32"], report)
+        for v, d in zip(invs, dinv):
+            _check_outputs(spec, w, v, d, RTOL["f32"], report)
         print("fp32 batching, error vs fp64 oracle:", report)
     finally:
         fn.release()
@@ -148,8 +161,8 @@ def test_batching_fp32_gather_fused_with_top0_every_element():
 
 def test_precision_bf16_full_size_every_element_of_16_invocations():
     """26 x 1,000,000 x 128 bf16 (6.7 GB), 128 lognormal invocations (~57k samples) in one
-    fused batch: every pooled and bottom column of 16 whole invocations (every eighth),
-    and the first top hidden layer (3456 -> 1024) of two of them."""
+    fused batch: every pooled and bottom column and every output of 16 whole invocations
+    (every eighth), and the first top hidden layer (3456 -> 1024) of two of them."""
     pool, fn, spec, invs, dinv, M = _fused_batch("c3")
     try:
         w = workload.weights_arrays(spec)
@@ -163,6 +176,7 @@ def test_precision_bf16_full_size_every_element_of_16_invocations():
             rc, rm = _check_invocation(spec, w, v, concat[base[i]:base[i + 1]], RTOL["bf16"], 8, report)
             if i in checked[:2]:
                 _check_top0(spec, w, fn, M, int(base[i]), v["batch"], rc, rm, RTOL["bf16"], report)
+            _check_outputs(spec, w, v, dinv[i], RTOL["bf16"], report)
         report["invocations"] = len(checked)
         report["samples"] = int(sum(invs[i]["batch"] for i in checked))
         print("bf16 precision, error vs fp64 oracle:", report)
