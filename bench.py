@@ -715,6 +715,26 @@ SERVE_KEYS = ("invocations_per_s", "p50_ms", "p99_ms", "warm_p50_ms", "warm_p99_
               "completed", "batches", "prepares", "evictions", "cold_requests", "max_inflight_batches", "wall_s")
 
 
+def cold_run_summary(reqs, results, n_fns):
+    """Setup and drain figures of one cold replay.  reqs: (fn, arrival_s, ...) per request;
+    results: sage_serve's per-request dicts (latency_ms, queue_ms, cold).  A function's
+    setup ends at its first launch (the earliest arrival + queueing time of its
+    requests); a cold request's time after setup is its completion minus the later of
+    its arrival and that first launch -- how fast a serving form works through the
+    requests that queued behind a setup, apart from the setup itself."""
+    first = {}
+    for q, x in zip(reqs, results):
+        t = q[1] + x["queue_ms"] / 1e3
+        first[q[0]] = min(first.get(q[0], t), t)
+    out = {"first_launch_s_by_function": [round(first.get(f, -1.0), 3) for f in range(n_fns)]}
+    drain = sorted((q[1] + x["latency_ms"] / 1e3 - max(q[1], first[q[0]])) * 1e3
+                   for q, x in zip(reqs, results) if x["cold"] and x["latency_ms"] >= 0)
+    if drain:
+        out["cold_after_setup_p50_ms"] = round(drain[len(drain) // 2], 3)
+        out["cold_after_setup_p99_ms"] = round(drain[min(len(drain) - 1, int(0.99 * len(drain)))], 3)
+    return out
+
+
 def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), repeats=1, **kw):
     """Replay one trace per mode on a fresh pool: cold (every function prepared at its
     first request: setup inside the latencies) or warm (every function resident and
@@ -730,6 +750,7 @@ def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), rep
     fkw = [workload.prepare_kwargs(s) for s in specs]
     res, outs = {}, {}
     order = list(modes) if repeats == 1 else [("discard", modes[0][1])] + list(modes) + list(reversed(modes))
+    lanes = kw.pop("lanes_per_fn", 2)
     for mode, mbi in order:
         pool = sage.Pool(device=0)
         held = []
@@ -737,8 +758,7 @@ def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), rep
             held = [pool.prepare(**workload.prepare_kwargs(s)) for s in specs]
             for h in held:
                 h.wait()
-        r, st = sage.serve(pool, fkw, reqs, max_batch_invocations=mbi, lanes_per_fn=kw.pop("lanes_per_fn", 2),
-                           **kw)
+        r, st = sage.serve(pool, fkw, reqs, max_batch_invocations=mbi, lanes_per_fn=lanes, **kw)
         outs[mode] = out.clone()
         for h in held:
             h.release()
@@ -748,18 +768,7 @@ def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), rep
         one = {k: (round(st[k], 3) if isinstance(st[k], float) else st[k]) for k in SERVE_KEYS}
         one["mean_batch_invocations"] = round(float(np.mean([x["batch_invocations"] for x in r])), 2)
         if not warm:
-            first = {}
-            for q, x in zip(reqs, r):
-                t = q[1] + x["queue_ms"] / 1e3
-                first[q[0]] = min(first.get(q[0], t), t)
-            one["first_launch_s_by_function"] = [round(first.get(f, -1.0), 3) for f in range(len(specs))]
-            # how fast each form serves once a function's setup is done: completion minus
-            # the later of arrival and the function's first launch, over the cold requests
-            drain = sorted((q[1] + x["latency_ms"] / 1e3 - max(q[1], first[q[0]])) * 1e3
-                           for q, x in zip(reqs, r) if x["cold"] and x["latency_ms"] >= 0)
-            if drain:
-                one["cold_after_setup_p50_ms"] = round(drain[len(drain) // 2], 3)
-                one["cold_after_setup_p99_ms"] = round(drain[min(len(drain) - 1, int(0.99 * len(drain)))], 3)
+            one.update(cold_run_summary(reqs, r, len(specs)))
         res.setdefault(mode, {"runs": []})["runs"].append(one)
     for mode, v in res.items():
         runs = v.pop("runs")

@@ -85,3 +85,20 @@ def test_oracle_timing_normalises_by_the_mean_invocation(monkeypatch):
     assert calls[0] == 30 and done == len(calls) and samples == sum(calls)
     # ~1000 samples/s / 20 samples per invocation = ~50 invocations/s
     assert 30.0 < rate < 55.0
+
+
+def test_cold_run_summary():
+    """A function's setup ends at its first launch; a cold request's time after setup is
+    its completion minus max(arrival, that launch)."""
+    # fn 0 ready at 1.0 s: requests at 0.1 (done 1.010), 0.5 (done 1.020), 1.2 warm (done 1.201)
+    # fn 1 ready at 0.3 s: request at 0.2 (done 0.305)
+    reqs = [(0, 0.1), (0, 0.5), (1, 0.2), (0, 1.2)]
+    res = [{"queue_ms": 900.0, "latency_ms": 910.0, "cold": 1},
+           {"queue_ms": 500.0, "latency_ms": 520.0, "cold": 1},
+           {"queue_ms": 100.0, "latency_ms": 105.0, "cold": 1},
+           {"queue_ms": 0.0, "latency_ms": 1.0, "cold": 0}]
+    s = bench.cold_run_summary(reqs, res, 3)
+    assert s["first_launch_s_by_function"] == [1.0, 0.3, -1.0]
+    # after setup: 10, 20 and 5 ms (the warm request is not counted): median 10, p99 20
+    assert abs(s["cold_after_setup_p50_ms"] - 10.0) < 1e-6
+    assert abs(s["cold_after_setup_p99_ms"] - 20.0) < 1e-6
