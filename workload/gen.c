@@ -43,10 +43,6 @@ uint64_t wl_mix64(uint64_t z) { return mix64_(z); }
 
 uint64_t wl_draw(uint64_t seed, uint64_t e) { return mix64_(seed + (e + 1) * WL_GAMMA); }
 
-static inline float wl_value(uint64_t seed, uint64_t e, float step) {
-    int32_t k = (int32_t)(mix64_(seed + (e + 1) * WL_GAMMA) >> 40) - 8388608;
-    return (float)k * step;
-}
 
 static inline uint16_t wl_bf16_rne(float f) {
     uint32_t u;
@@ -59,12 +55,16 @@ static inline uint16_t wl_bf16_rne(float f) {
 __attribute__((target_clones("arch=x86-64-v4", "arch=x86-64-v3", "default")))
 void wl_fill_stream(void* dst, int dtype, uint64_t seed, float bound, uint64_t first, size_t n) {
     float step = bound / 8388608.0f;
+    /* the SplitMix64 state of element e is seed + (e + 1) * gamma: advanced by one
+     * addition per element (the same values as computing it from e each time) */
+    uint64_t z = seed + (first + 1) * WL_GAMMA;
     if (dtype == 0) {
         float* d = (float*)dst;
-        for (size_t i = 0; i < n; ++i) d[i] = wl_value(seed, first + i, step);
+        for (size_t i = 0; i < n; ++i, z += WL_GAMMA) d[i] = (float)((int32_t)(mix64_(z) >> 40) - 8388608) * step;
     } else {
         uint16_t* d = (uint16_t*)dst;
-        for (size_t i = 0; i < n; ++i) d[i] = wl_bf16_rne(wl_value(seed, first + i, step));
+        for (size_t i = 0; i < n; ++i, z += WL_GAMMA)
+            d[i] = wl_bf16_rne((float)((int32_t)(mix64_(z) >> 40) - 8388608) * step);
     }
 }
 
