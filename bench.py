@@ -657,16 +657,13 @@ def run_ours(args, rank, world, local_rank):
     return line, spec, invs
 
 
-def staging_warm_host(spec, dev, warm_s=1.5):
-    """The same function staged again by a fresh pool after every host core has run the
-    producer for warm_s seconds.  On the benchmark boxes an idle host core comes back
-    several times slower and needs seconds of load to reach speed, so the cold setup
-    above is bound by the producers' cold cores; this shows what the staging pipeline
-    moves once they are at speed."""
+def warm_host_cores(seconds):
+    """Run the input generator on every host core for `seconds` (scratch buffers only):
+    on the benchmark boxes idle host cores come back several times slower and need
+    seconds of load to reach speed."""
     import threading
-    import paper_2404_14691_b300 as sage
     lib = workload.lib()
-    stop = time.perf_counter() + warm_s
+    stop = time.perf_counter() + seconds
 
     def spin(k):
         b = np.empty(1 << 20, np.uint16)
@@ -678,6 +675,16 @@ def staging_warm_host(spec, dev, warm_s=1.5):
         t.start()
     for t in ths:
         t.join()
+
+
+def staging_warm_host(spec, dev, warm_s=1.5):
+    """The same function staged again by a fresh pool after every host core has run the
+    producer for warm_s seconds.  On the benchmark boxes an idle host core comes back
+    several times slower and needs seconds of load to reach speed, so the cold setup
+    above is bound by the producers' cold cores; this shows what the staging pipeline
+    moves once they are at speed."""
+    import paper_2404_14691_b300 as sage
+    warm_host_cores(warm_s)
     pool = sage.Pool(device=dev)
     t0 = time.perf_counter()
     fn = pool.prepare(**workload.prepare_kwargs(spec))
@@ -779,6 +786,7 @@ def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), rep
     (of the first mode) warms the process -- the CUDA memory pool, host allocations --
     and the modes then run in the order A B B A, each reporting the mean of its two runs
     (per-run values under "runs"), so that neither profits from its place in the order.
+    Before each cold run the host cores run the producer for 1.5 s (warm_host_cores).
     Every cold run also reports when each function's first batch launched (its setup
     finished), in seconds from the start of the replay.  Returns ({mode: stats},
     {mode: outputs})."""
@@ -788,6 +796,10 @@ def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), rep
     order = list(modes) if repeats == 1 else [("discard", modes[0][1])] + list(modes) + list(reversed(modes))
     lanes = kw.pop("lanes_per_fn", 2)
     for mode, mbi in order:
+        if not warm:
+            # every cold run starts from host cores at speed, so that the modes compare
+            # their setups rather than the host's warm-up
+            warm_host_cores(1.5)
         pool = sage.Pool(device=0)
         held = []
         if warm:
