@@ -677,7 +677,7 @@ def warm_host_cores(seconds):
         t.join()
 
 
-def staging_warm_host(spec, dev, warm_s=1.5):
+def staging_warm_host(spec, dev, warm_s=3.0):
     """The same function staged again by a fresh pool after every host core has run the
     producer for warm_s seconds.  On the benchmark boxes an idle host core comes back
     several times slower and needs seconds of load to reach speed, so the cold setup
