@@ -171,6 +171,10 @@ typedef struct {
     int64_t num_indices;           /* optional: offsets[T*B] - offsets[0] when known on the host, else 0;
                                       used only for the byte count of the kernel-timing record */
 } sage_invocation;
+/* The device offsets are read only by the kernels, never on the host, so they are
+ * not checked: they must never decrease and must stay inside the indices buffer
+ * (a bad offset reads outside the caller's indices).  Row indices outside their
+ * table are checked on the device (skipped, SAGE_ERR_BOUNDS from sage_fn_check). */
 
 /* The same invocation with HOST buffers (Writable data loaded to the GPU and the
  * result dumped back, SageLoadToGPU / SageDumpToDB of Sec. 5.2). */
@@ -182,6 +186,9 @@ typedef struct {
     int64_t num_indices;           /* == offsets[num_tables*B] */
     float* out;                    /* host [B] */
 } sage_host_invocation;
+/* Host offsets are checked before anything is copied: offsets[0] == 0, never
+ * decreasing, offsets[num_tables*B] == num_indices; otherwise the call (and
+ * sage_serve, for any request) returns SAGE_ERR_INVALID. */
 
 typedef struct {
     size_t budget_bytes;

@@ -19,6 +19,12 @@ void set_last_error(const char* msg);
 // Asynchronous fused batch from host buffers on a chosen workspace slot (-1: next in turn).
 sage_status host_batch_async(sage_fn f, const sage_host_invocation* invs, int n, cudaStream_t s, int slot);
 
+// A host invocation's bags lie inside its indices: offsets[0] == 0, the offsets
+// never decrease, and offsets[T * B] == num_indices (an empty batch passes).  Both
+// host entry points check this before any copy, so a malformed request is refused
+// instead of reading outside the indices it copied.
+bool host_csr_valid(const sage_host_invocation& v, int T);
+
 // Kernels launched by this library so far (all pools, all threads).
 void count_launch(int n = 1);
 int64_t launches();

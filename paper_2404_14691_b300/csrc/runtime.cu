@@ -1595,6 +1595,17 @@ sage_status fn_export(sage_fn f, VmmBlock* tables, VmmBlock* weights) {
   return SAGE_OK;
 }
 
+bool host_csr_valid(const sage_host_invocation& v, int T) {
+  if (v.batch <= 0) return true;
+  if (!v.offsets || T < 1) return false;
+  const size_t nb = static_cast<size_t>(T) * v.batch;
+  const int64_t* o = v.offsets;
+  if (o[0] != 0 || o[nb] != v.num_indices) return false;
+  bool bad = false;  // one pass without early exit: the compiler vectorises it
+  for (size_t j = 0; j < nb; ++j) bad |= o[j + 1] < o[j];
+  return !bad;
+}
+
 }  // namespace sage
 
 
@@ -1619,7 +1630,10 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
     if (v.batch == 0) continue;
     if (!v.dense || !v.offsets || !v.out || (v.num_indices > 0 && !v.indices))
       return fail(SAGE_ERR_INVALID, "invocation %d: null buffer", i);
-    nd += static_cast<size_t>(v.batch) * e->n_dense * 4;
+    if (!host_csr_valid(v, e->T))
+      return fail(SAGE_ERR_INVALID, "invocation %d: offsets must start at 0, never decrease and end at num_indices",
+                  i);
+    nd +=static_cast<size_t>(v.batch) * e->n_dense * 4;
     ni += static_cast<size_t>(v.num_indices) * 4;
     no += (static_cast<size_t>(e->T) * v.batch + 1) * 8;
     nu += static_cast<size_t>(v.batch) * 4;

@@ -74,6 +74,9 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
   for (int i = 0; i < n; ++i) {
     if (reqs[i].fn < 0 || reqs[i].fn >= n_fns || reqs[i].inv.batch < 0)
       return sage::set_last_error("request with a bad function index or batch"), SAGE_ERR_INVALID;
+    if (!sage::host_csr_valid(reqs[i].inv, fns[reqs[i].fn].num_tables))
+      return sage::set_last_error("request whose offsets do not start at 0, decrease or do not end at num_indices"),
+             SAGE_ERR_INVALID;
     results[i] = sage_request_result{-1.0, -1.0, -1.0, 0, 0, SAGE_PENDING};
   }
   std::unique_ptr<sage::Partition> part;

@@ -352,6 +352,58 @@ def test_host_allocator_buffers_serve_host_invocations(pool):
         fn.release()
 
 
+def _bad_offsets(v):
+    """Malformed CSR variants of an invocation's offsets.  Each one keeps every bag
+    inside [0, num_indices], so even an unchecked run would read only copied indices."""
+    off = v["offsets"]
+    n = v["indices"].size
+    assert off[0] == 0 and off[-1] == n and n > 4
+    start = off.copy()
+    start[0] = 1                                    # does not start at 0
+    short = off.copy()
+    short[-1] = n - 1                               # does not end at num_indices
+    dec = off.copy()
+    j = int(np.argmax(off[1:-1] > 0)) + 1           # an inner offset above 0
+    dec[j] = 0 if dec[j - 1] > 0 else dec[j]        # a step down
+    if np.all(np.diff(dec) >= 0):
+        dec[j + 1] = dec[j] - 1 if dec[j] > 0 else dec[j + 1]
+    assert np.any(np.diff(dec) < 0)
+    return {"start": start, "end": short, "decreasing": dec}
+
+
+def test_host_offsets_are_checked_before_any_copy(pool):
+    """Host-buffer batches and served requests with offsets that do not start at 0, step
+    down, or do not end at num_indices are refused on the host (SAGE_ERR_INVALID), and a
+    good invocation still runs afterwards."""
+    spec = spec_small("bf16", key="rt_badcsr")
+    fn = prepare(pool, spec)
+    try:
+        v = workload.make_invocation(spec, 64, seed=11)
+        out = np.full(64, np.nan, np.float32)
+        launches0 = sage.kernel_launches()
+        for name, off in _bad_offsets(v).items():
+            with pytest.raises(sage.SageError) as e:
+                fn.invoke_batch_host([(64, v["dense"].ctypes.data, v["indices"].ctypes.data, off.ctypes.data,
+                                       v["indices"].size, out.ctypes.data)])
+            assert e.value.status == -1, name
+            assert "offsets" in str(e.value), name
+            with pytest.raises(sage.SageError) as e:
+                sage.serve(pool, [workload.prepare_kwargs(spec)],
+                           [(0, 0.0, 64, v["dense"].ctypes.data, v["indices"].ctypes.data, off.ctypes.data,
+                             v["indices"].size, out.ctypes.data)])
+            assert e.value.status == -1, name
+        assert sage.kernel_launches() == launches0
+        assert np.isnan(out).all()
+        fn.invoke_batch_host([(64, v["dense"].ctypes.data, v["indices"].ctypes.data, v["offsets"].ctypes.data,
+                               v["indices"].size, out.ctypes.data)])
+        d = DevInvocation(v)
+        fn.invoke(*d.args())
+        _torch().cuda.synchronize()
+        assert np.array_equal(out, d.out.cpu().numpy())
+    finally:
+        fn.release()
+
+
 def test_multistage_exit_restages_from_the_host_cache():
     """Stage 2 of the multi-stage exit: released read-only data waits in host memory and a
     later prepare re-stages it from there without calling the producer."""
