@@ -27,17 +27,6 @@ struct Acc {
 
 __device__ __forceinline__ uint4 ldg_nc_v4(const uint4* p) { return __ldg(p); }
 
-// The same load with a 256-byte L2 fetch hint: on a miss the L2 brings in the whole
-// 256-byte row, which the lane group reads in two 128-byte halves (fp32 lane-group
-// kernel: batching step 0.186 against 0.191 ms; the bf16 kernel lost 1% with it).
-__device__ __forceinline__ uint4 ldg_nc_v4_row256(const uint4* p) {
-  uint4 r;
-  asm("ld.global.nc.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
-      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-      : "l"(p));
-  return r;
-}
-
 // The warp's next unit of work from the launch's `next` counter (called by all lanes).
 __device__ __forceinline__ uint32_t claim(unsigned* work) {
   uint32_t q = 0;
@@ -421,7 +410,7 @@ __global__ void __launch_bounds__(256) gather_group_kernel(const __grid_constant
           }
           const uint4* src = reinterpret_cast<const uint4*>(base + static_cast<size_t>(ok[u] ? row : 0) * row_bytes);
 #pragma unroll
-          for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4_row256(src + w) : make_uint4(0, 0, 0, 0);
+          for (int w = 0; w < VPL; ++w) v[u][w] = ok[u] ? ldg_nc_v4(src + w) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
