@@ -177,32 +177,75 @@ def traffic_for(kind: str, workload_name: str):
 
 # ------------------------------------------------------------------ CPU oracle
 
-def oracle_timing(spec, invs, budget_s: float, threads: int, start: int = 0):
-    """The fp64 CPU oracle on whole invocations of the workload, taken in order from
-    invs[start] (cycling), until about budget_s seconds have passed (at least one).
+def stratified_order(batches):
+    """Invocation indices sorted by batch size, then visited in van der Corput order over
+    that sorted list (positions 0, 1/2, 1/4, 3/4, 1/8, ... of it), so that every prefix of
+    the order spreads over the workload's size distribution.  A time-bounded sample of the
+    oracle that stops after a prefix then holds small and large invocations in the
+    workload's proportions (the oracle's samples per second depend on the batch size)."""
+    n = len(batches)
+    by_size = sorted(range(n), key=lambda i: (batches[i], i))
+    order, seen, k = [], set(), 0
+    while len(order) < n:
+        k += 1
+        x, f, j = 0.0, 0.5, k
+        while j:
+            x += f * (j & 1)
+            j >>= 1
+            f *= 0.5
+        pos = int(x * n)
+        if pos not in seen:
+            seen.add(pos)
+            order.append(by_size[pos])
+    return order
 
-    Returns (invocations_per_s, done, samples, seconds).  Invocations differ in size,
-    so the rate is the oracle's samples per second divided by the workload's mean
-    samples per invocation: the invocations per second it would sustain on this
-    workload's mix, whichever invocations the sample happened to hold.  Both the
-    benchmark line's cpu_baseline and the reference arm use this one function."""
+
+def oracle_rate(records, batches):
+    """Invocations per second of the oracle over the whole workload, from timed
+    invocations: `records` = [(batch, seconds)], `batches` = every invocation's batch.
+
+    The oracle's time per invocation is a fixed part (its per-call set-up) plus a part
+    per sample, so samples per second depend on which invocations a time-bounded sample
+    held.  A least-squares fit of seconds = c + batch * t over the records predicts the
+    whole workload's time, N * c + sum(batches) * t, and the rate is N over that.  With
+    fewer than two distinct batch sizes, or a fit with a negative term, c = 0.
+    Returns (rate, c, t)."""
+    b = np.array([r[0] for r in records], np.float64)
+    y = np.array([r[1] for r in records], np.float64)
+    c, t = 0.0, float(y.sum() / max(1.0, b.sum()))
+    if len(set(b.tolist())) >= 2:
+        A = np.stack([np.ones_like(b), b], axis=1)
+        (c1, t1), *_ = np.linalg.lstsq(A, y, rcond=None)
+        if c1 >= 0 and t1 > 0:
+            c, t = float(c1), float(t1)
+    total = len(batches) * c + float(np.sum(batches)) * t
+    return len(batches) / total, c, t
+
+
+def oracle_timing(spec, invs, budget_s: float, threads: int, start: int = 0):
+    """The fp64 CPU oracle on whole invocations of the workload, taken in the stratified
+    order (stratified_order) from its position `start` (cycling), until about budget_s
+    seconds have passed (at least one).
+
+    Returns (records, seconds): records = [(batch, seconds)] per timed invocation, for
+    oracle_rate.  Both the benchmark line's cpu_baseline and the reference arm time the
+    oracle with this one function and turn the records into a rate with oracle_rate."""
     import oracle
     w = workload.weights_arrays(spec)
     src = lambda t, r: workload.table_rows(spec, t, r)
-    mean_batch = float(np.mean([v["batch"] for v in invs]))
+    order = stratified_order([v["batch"] for v in invs])
+    records = []
     t0 = time.perf_counter()
-    done = samples = 0
     k = start
     while True:
-        v = invs[k % len(invs)]
+        v = invs[order[k % len(invs)]]
+        t1 = time.perf_counter()
         oracle.forward(spec, w, v, row_source=src, n_threads=threads, want_pooled=False)
+        records.append((v["batch"], time.perf_counter() - t1))
         k += 1
-        done += 1
-        samples += v["batch"]
         if time.perf_counter() - t0 > budget_s:
             break
-    el = time.perf_counter() - t0
-    return samples / el / mean_batch, done, samples, el
+    return records, time.perf_counter() - t0
 
 
 def _avg_launch_s(nl, tms):
@@ -1205,42 +1248,52 @@ def run_share(args):
 
 def cpu_baseline(spec, invs, budget_s):
     threads = os.cpu_count() or 1
-    rate, done, samples, el = oracle_timing(spec, invs, budget_s, threads)
+    # the reference arm times only after its warm-up steps; give the host cores the same
+    warm_host_cores(1.5)
+    records, el = oracle_timing(spec, invs, budget_s, threads)
+    batches = [v["batch"] for v in invs]
+    rate, c, t = oracle_rate(records, batches)
     return {"value": round(rate, 4), "unit": "invocations/s", "cores": threads, "kind": "oracle",
-            "sample": "%d whole invocations of the step's %d (%d samples) in %.1f s, fp64 C oracle, %d threads; "
-                      "invocations/s = samples/s / the step's mean samples per invocation"
-                      % (done, len(invs), samples, el, threads)}
+            "sample": "%d whole invocations of the step's %d (%d samples, taken across the batch-size mix) in "
+                      "%.1f s after 1.5 s of host warm-up, fp64 C oracle, %d threads; invocations/s = the step's %d invocations over their "
+                      "predicted oracle time, from a least-squares fit of %.1f ms per invocation + %.3f ms per "
+                      "sample to the timed ones"
+                      % (len(records), len(invs), sum(r[0] for r in records), el, threads, len(invs),
+                         c * 1e3, t * 1e3)}
 
 
 def run_reference(args, rank, world):
     """The CPU oracle timed as it stands on this workload (rank 0 only): each step is a
-    bounded sample of whole invocations, continuing through the step's invocations."""
+    bounded sample of whole invocations, continuing through the workload's invocations
+    in the stratified order; the rate comes from the timed steps' invocations (oracle_rate)."""
     spec, invs, desc = make_workload(args.workload, 0)
     threads = os.cpu_count() or 1
     budget_per_step = min(10.0, 150.0 / max(1, args.steps + args.warmup))
     k = 0
-    done = samples = 0
+    records = []
     t_total = 0.0
     for s in range(args.warmup + args.steps):
-        r, n, smp, el = oracle_timing(spec, invs, budget_per_step, threads, start=k)
-        k += n
+        rec, el = oracle_timing(spec, invs, budget_per_step, threads, start=k)
+        k += len(rec)
         if s >= args.warmup:
-            done += n
-            samples += smp
+            records += rec
             t_total += el
-    mean_batch = float(np.mean([v["batch"] for v in invs]))
-    rate = samples / t_total / mean_batch
-    M = int(sum(v["batch"] for v in invs))
+    batches = [v["batch"] for v in invs]
+    rate, c, t = oracle_rate(records, batches)
+    M = int(sum(batches))
     line = {"impl": "reference", "metric": METRIC, "value": round(rate, 4), "unit": "invocations/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(t_total / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator; tables, weights, dense, Zipf bags)",
             "config": config_of(desc, len(invs), M, n_indices(invs), world),
             "cpu_baseline": {"value": round(rate, 4), "unit": "invocations/s", "cores": threads, "kind": "oracle",
-                             "sample": "each step: whole invocations of the workload for ~%.2f s (%d in total, %d "
-                                       "samples), fp64 C oracle, %d threads; invocations/s = samples/s / the "
-                                       "workload's mean samples per invocation"
-                                       % (budget_per_step, done, samples, threads)},
+                             "sample": "each step: whole invocations of the workload for ~%.2f s (%d timed in "
+                                       "total, %d samples), fp64 C oracle, %d threads; invocations/s = the "
+                                       "workload's %d invocations over their predicted oracle time, from a "
+                                       "least-squares fit of %.1f ms per invocation + %.3f ms per sample to the "
+                                       "timed ones"
+                                       % (budget_per_step, len(records), sum(r[0] for r in records), threads,
+                                          len(invs), c * 1e3, t * 1e3)},
             "e2e": {"value": round(rate, 4), "unit": "invocations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     return line

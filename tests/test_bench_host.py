@@ -67,24 +67,54 @@ def test_roofline_of_each_kernel_kind():
     assert a["bound"] == "alu" and abs(a["peak"] - 148 * 128 * 2 * 2000e6 / 1e12) < 0.01
 
 
-def test_oracle_timing_normalises_by_the_mean_invocation(monkeypatch):
-    """Both oracle legs (cpu_baseline and the reference arm) report samples/s divided by
-    the workload's mean samples per invocation, whichever invocations they timed."""
+def test_stratified_order_is_a_permutation_spread_over_sizes():
+    """Every invocation once; the first four cover the quartiles of the size mix."""
+    sizes = [5, 1, 9, 3, 7, 2, 8, 4, 6, 10, 11, 12]
+    o = bench.stratified_order(sizes)
+    assert sorted(o) == list(range(len(sizes)))
+    first = sorted(sizes[i] for i in o[:4])
+    ranks = sorted(sorted(sizes).index(v) for v in first)
+    assert ranks[0] < 3 and ranks[-1] >= 9 and len(set(r // 3 for r in ranks)) == 4
+
+
+def test_oracle_rate_recovers_the_whole_mix_from_any_prefix():
+    """With a per-invocation cost c + B * t, the fit over any timed prefix (two or more
+    sizes) predicts the whole workload's time exactly, so both oracle legs agree however
+    many invocations their budgets allowed."""
+    c, t = 0.030, 0.0019
+    batches = [1, 3, 17, 40, 90, 250, 400, 700, 1500, 4096]
+    want = len(batches) / sum(c + b * t for b in batches)
+    order = bench.stratified_order(batches)
+    for m in (2, 3, 5, len(batches)):
+        recs = [(batches[i], c + batches[i] * t) for i in order[:m]]
+        rate, c_fit, t_fit = bench.oracle_rate(recs, batches)
+        assert abs(rate / want - 1) < 1e-9 and abs(c_fit - c) < 1e-9 and abs(t_fit - t) < 1e-12
+    # one size only: no intercept can be fitted; the per-sample rate is used (c = 0)
+    rate, c_fit, _ = bench.oracle_rate([(100, 0.2), (100, 0.2)], [100, 100, 100])
+    assert c_fit == 0.0 and abs(rate - 5.0) < 1e-9
+
+
+def test_oracle_timing_records_each_invocation(monkeypatch):
+    """oracle_timing walks the stratified order from `start` and times every invocation."""
     import time as _t
     import oracle
     calls = []
 
     def fake_forward(spec, w, v, **kw):
         calls.append(v["batch"])
-        _t.sleep(0.001 * v["batch"])        # 1 ms per sample
+        _t.sleep(0.002 + 0.0005 * v["batch"])
 
     monkeypatch.setattr(oracle, "forward", fake_forward)
     monkeypatch.setattr(bench.workload, "weights_arrays", lambda spec: None)
-    invs = [{"batch": 10}, {"batch": 30}]          # mean 20 samples
-    rate, done, samples, el = bench.oracle_timing(None, invs, 0.15, 1, start=1)
-    assert calls[0] == 30 and done == len(calls) and samples == sum(calls)
-    # ~1000 samples/s / 20 samples per invocation = ~50 invocations/s
-    assert 30.0 < rate < 55.0
+    invs = [{"batch": b} for b in (10, 30, 50, 70)]
+    order = bench.stratified_order([v["batch"] for v in invs])
+    recs, el = bench.oracle_timing(None, invs, 0.15, 1, start=1)
+    assert [r[0] for r in recs] == calls
+    assert calls[:3] == [invs[order[(1 + k) % 4]]["batch"] for k in range(3)]
+    assert all(r[1] >= 0.002 + 0.0005 * r[0] for r in recs) and el >= sum(r[1] for r in recs)
+    rate, c, t = bench.oracle_rate(recs, [v["batch"] for v in invs])
+    want = 4 / sum(0.002 + 0.0005 * v["batch"] for v in invs)
+    assert 0.6 * want < rate <= 1.05 * want
 
 
 def test_cold_run_summary():
