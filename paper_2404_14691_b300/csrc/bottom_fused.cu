@@ -437,25 +437,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, 2 * BN);
 }
 
-int g_sms_b01 = 0;
-
 // yh / yl / ldy: layer 1's output, or layer 2's when `w2h` is given (N2 outputs).
 template <int BN, int NST, bool L2>
 cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, const float* b0, int N1,
                        const float* w1h, const float* w1l, const float* b1, float* yh, float* yl, int ldy, int* err,
                        cudaStream_t s, const float* w2h, const float* w2l, const float* b2, int N2) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(bottom01_kernel<BN, NST, L2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         B01Cfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  if (!g_sms_b01) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_b01, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(bottom01_kernel<BN, NST, L2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, B01Cfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   const int nout = L2 ? N2 : N1;
   CUtensorMap tbh, tbl, tyh, tyl;
   Layer2 l2{};
@@ -464,13 +457,14 @@ cudaError_t launch_b01(const InvTable& tab, int K0, int N0, const float* W0, con
     return cudaErrorInvalidValue;
   const int tiles = (N1 / BN) * ((tab.M + kBM - 1) / kBM);
   if (L2) {
-    if (BN != N1 || tiles > g_sms_b01) return cudaErrorInvalidValue;  // one whole-row tile per CTA
+    if (BN != N1 || tiles > device_sms()) return cudaErrorInvalidValue;  // one whole-row tile per CTA
     if (!make_tmap_2d(&l2.wh, 0, w2h, N2, N1, N1, kBK, N2) || !make_tmap_2d(&l2.wl, 0, w2l, N2, N1, N1, kBK, N2))
       return cudaErrorInvalidValue;
     l2.b = b2;
     l2.n = N2;
   }
-  const int grid = tiles < g_sms_b01 ? tiles : g_sms_b01;
+  const int sms_n = device_sms();
+  const int grid = tiles < sms_n ? tiles : sms_n;
   bottom01_kernel<BN, NST, L2><<<grid, kThreads, B01Cfg<BN, NST>::SMEM, s>>>(
       tbh, tbl, tyh, tyl, tab, K0, N0, W0, b0, N1, b1, yh, yl, ldy, err, l2);
   count_launch();
@@ -497,12 +491,7 @@ int bottom01_candidates(GemmCfg* out, int max) {
 }
 
 bool bottom012_fusable(int N1, int N2, int M) {
-  if (!g_sms_b01) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_b01, cudaDevAttrMultiProcessorCount, dev);
-  }
-  return N1 == 256 && N2 >= 32 && N2 <= 256 && N2 % 32 == 0 && (M + kBM - 1) / kBM <= g_sms_b01;
+  return N1 == 256 && N2 >= 32 && N2 <= 256 && N2 % 32 == 0 && (M + kBM - 1) / kBM <= device_sms();
 }
 
 GemmCfg bottom01_default(int N1) {

@@ -302,16 +302,24 @@ __global__ void __launch_bounds__(256) gather_kernel(const __grid_constant__ Gat
 
 template <bool BF16, int LPR, int VPL, int U, int RUN>
 cudaError_t launch_one(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
-  static int blocks_per_sm = -1, sms = 0;
-  if (blocks_per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(gather_kernel<BF16, LPR, VPL, U, RUN>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxL1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_kernel<BF16, LPR, VPL, U, RUN>, 256, 0);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
+  // per device: the largest L1 carve-out (no shared memory is used) and the occupancy
+  static DeviceOnce once;
+  static int bps[kMaxDevices];
+  int dev = 0;
+  if (cudaError_t e = device_once(
+          once,
+          [](int d) {
+            cudaFuncSetAttribute(gather_kernel<BF16, LPR, VPL, U, RUN>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxL1);
+            int b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_kernel<BF16, LPR, VPL, U, RUN>, 256, 0);
+            bps[d] = b < 1 ? 1 : b;
+            return cudaSuccess;
+          },
+          &dev);
+      e != cudaSuccess)
+    return e;
+  const int blocks_per_sm = bps[dev], sms = device_sms();
   const int64_t bags = static_cast<int64_t>(a.T) * tab.M;
   if (bags == 0) return cudaSuccess;
   // runs of up to RUN bags per warp once there are several bags per resident warp;
@@ -465,16 +473,24 @@ __global__ void __launch_bounds__(256) gather_group_kernel(const __grid_constant
 
 template <bool BF16, int LPR, int VPL, int U>
 cudaError_t launch_group(const GatherArgs& a, const InvTable& tab, cudaStream_t s) {
-  static int blocks_per_sm = -1, sms = 0;
-  if (blocks_per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(gather_group_kernel<BF16, LPR, VPL, U>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxL1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, gather_group_kernel<BF16, LPR, VPL, U>, 256, 0);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
+  // per device: the largest L1 carve-out (no shared memory is used) and the occupancy
+  static DeviceOnce once;
+  static int bps[kMaxDevices];
+  int dev = 0;
+  if (cudaError_t e = device_once(
+          once,
+          [](int d) {
+            cudaFuncSetAttribute(gather_group_kernel<BF16, LPR, VPL, U>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxL1);
+            int b = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, gather_group_kernel<BF16, LPR, VPL, U>, 256, 0);
+            bps[d] = b < 1 ? 1 : b;
+            return cudaSuccess;
+          },
+          &dev);
+      e != cudaSuccess)
+    return e;
+  const int blocks_per_sm = bps[dev], sms = device_sms();
   constexpr int NG = 32 / LPR;
   const int64_t bags = static_cast<int64_t>(a.T) * tab.M;
   if (bags == 0) return cudaSuccess;

@@ -350,15 +350,16 @@ cudaError_t launch_nh(const GatherArgs& a, const InvTable& tab, int K0, const CU
                       const CUtensorMap& txh, const CUtensorMap& txl, const float* b0, float* yh, float* yl, int ldy,
                       int* err, cudaStream_t s) {
   using C = GTCfg<NH>;
-  static int sms = 0;
   auto kern = gather_top0_kernel<NH, kP, kU>;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gather_top0_kernel<NH, kP, kU>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    C::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   const int tiles = (tab.M + kBM - 1) / kBM;
+  const int sms = device_sms();
   const int grid = tiles < sms ? tiles : sms;
   kern<<<grid, 192 + 32 * kP, C::SMEM, s>>>(tbh, tbl, txh, txl, a, tab, K0, b0, yh, yl, ldy, err);
   count_launch();

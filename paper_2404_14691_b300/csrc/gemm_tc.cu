@@ -354,13 +354,13 @@ bool make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int 
 template <int BN, int NST>
 cudaError_t launch_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias, int relu,
                       void* y, int ldy, int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TcCfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tc_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap ta, tb;
   if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
   dim3 grid(N / BN, (M + kBM - 1) / kBM);
@@ -370,28 +370,22 @@ cudaError_t launch_bn(int M, int N, int K, const void* x, int ldx, const void* W
   return cudaGetLastError();
 }
 
-int g_sms_pt = 0;
-
 template <int BN, int NST>
 cudaError_t launch_persistent_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias,
                                  int relu, void* y, int ldy, int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_persistent_kernel<BN, NST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  if (!g_sms_pt) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_pt, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tc_persistent_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap ta, tb, tb2;
   if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN) || !make_map(&tb2, W, N, K, K, BN / 2))
     return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
-  const int grid = tiles < g_sms_pt ? tiles : g_sms_pt;
+  const int sms_n = device_sms();
+  const int grid = tiles < sms_n ? tiles : sms_n;
   gemm_tc_persistent_kernel<BN, NST><<<grid, 192, TcCfg<BN, NST>::SMEM, s>>>(
       ta, tb, tb2, M, N, K, bias, relu, static_cast<__nv_bfloat16*>(y), ldy, err);
   count_launch();
@@ -401,22 +395,18 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const void* x, int ldx, co
 template <int BN, int NST>
 cudaError_t launch_persistent_head_bn(int M, int N, int K, const void* x, int ldx, const void* W, const float* bias,
                                       int relu, int* err, cudaStream_t s, const HeadParams& hp) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_persistent_head_kernel<BN, NST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  if (!g_sms_pt) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_pt, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tc_persistent_head_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap ta, tb;
   if (!make_map(&ta, x, M, K, ldx, kBM) || !make_map(&tb, W, N, K, K, BN)) return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
-  const int grid = tiles < g_sms_pt ? tiles : g_sms_pt;
+  const int sms_n = device_sms();
+  const int grid = tiles < sms_n ? tiles : sms_n;
   gemm_tc_persistent_head_kernel<BN, NST><<<grid, 192, TcCfg<BN, NST>::SMEM, s>>>(ta, tb, M, N, K, bias, relu, err,
                                                                                   hp);
   count_launch();
@@ -443,8 +433,6 @@ cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const void* x, int ldx, c
     return launch_persistent_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return cudaErrorInvalidValue;
 }
-
-int g_sms = 0;
 
 }  // namespace
 
@@ -519,18 +507,14 @@ cudaError_t launch_linear_bf16_tc(int M, int N, int K, const void* x, int ldx, c
       (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(W) & 15) ||
       (reinterpret_cast<uintptr_t>(y) & 15))
     return cudaErrorInvalidValue;
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  const int sms_n = device_sms();
   if (cfg.bn) {
     if (N % cfg.bn) return cudaErrorInvalidValue;
     return launch_cfg(cfg, M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   }
   const int mt = (M + kBM - 1) / kBM;
-  if (N % 256 == 0 && mt * (N / 256) >= g_sms) return launch_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
-  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 256 == 0 && mt * (N / 256) >= sms_n) return launch_bn<256, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 128 == 0 && mt * (N / 128) >= sms_n) return launch_bn<128, 6>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return launch_bn<64, 8>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
 }
 

@@ -580,13 +580,13 @@ template <int BN, int NST>
 cudaError_t launch_presplit_bn(int M, int N, int K, const float* xh, const float* xl, int ldx, const float* wh,
                                const float* wl, const float* bias, int relu, float* yh, float* yl, int ldy, int* err,
                                cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_presplit_kernel<BN, NST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tf32x3_presplit_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap tah, tal, tbh, tbl;
   if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
       !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN))
@@ -598,24 +598,17 @@ cudaError_t launch_presplit_bn(int M, int N, int K, const float* xh, const float
   return cudaGetLastError();
 }
 
-int g_sms_p = 0;
-
 template <int BN, int NST>
 cudaError_t launch_persistent_bn(int M, int N, int K, const float* xh, const float* xl, int ldx, const float* wh,
                                  const float* wl, const float* bias, int relu, float* yh, float* yl, int ldy,
                                  int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_persistent_kernel<BN, NST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  if (!g_sms_p) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_p, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tf32x3_persistent_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap tah, tal, tbh, tbl, tyh, tyl, tbh2, tbl2;
   if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
       !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN) ||
@@ -623,7 +616,8 @@ cudaError_t launch_persistent_bn(int M, int N, int K, const float* xh, const flo
       !make_tmap_2d(&tyh, 0, yh, M, N, ldy, 32, 32) || !make_tmap_2d(&tyl, 0, yl, M, N, ldy, 32, 32))
     return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
-  const int grid = tiles < g_sms_p ? tiles : g_sms_p;
+  const int sms_n = device_sms();
+  const int grid = tiles < sms_n ? tiles : sms_n;
   gemm_tf32x3_persistent_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(
       tah, tal, tbh, tbl, tyh, tyl, tbh2, tbl2, M, N, K, bias, relu, yh, yl, ldy, err);
   count_launch();
@@ -634,24 +628,20 @@ template <int BN, int NST>
 cudaError_t launch_persistent_head_bn(int M, int N, int K, const float* xh, const float* xl, int ldx,
                                       const float* wh, const float* wl, const float* bias, int relu, int* err,
                                       cudaStream_t s, const HeadParams& hp) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_persistent_head_kernel<BN, NST>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  if (!g_sms_p) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms_p, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tf32x3_persistent_head_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap tah, tal, tbh, tbl;
   if (!make_tmap_2d(&tah, 0, xh, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tal, 0, xl, M, K, ldx, kBK, kBM) ||
       !make_tmap_2d(&tbh, 0, wh, N, K, K, kBK, BN) || !make_tmap_2d(&tbl, 0, wl, N, K, K, kBK, BN))
     return cudaErrorInvalidValue;
   const int tiles = (N / BN) * ((M + kBM - 1) / kBM);
-  const int grid = tiles < g_sms_p ? tiles : g_sms_p;
+  const int sms_n = device_sms();
+  const int grid = tiles < sms_n ? tiles : sms_n;
   gemm_tf32x3_persistent_head_kernel<BN, NST><<<grid, 192, Tf32Cfg<BN, NST>::SMEM, s>>>(
       tah, tal, tbh, tbl, M, N, K, bias, relu, err, hp);
   count_launch();
@@ -678,13 +668,13 @@ cudaError_t launch_presplit_cfg(GemmCfg c, int M, int N, int K, const float* xh,
 template <int BN, int NST>
 cudaError_t launch_bn(int M, int N, int K, const float* x, int ldx, const float* W, const float* bias, int relu,
                       float* y, int ldy, int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_kernel<BN, NST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Tf32Cfg<BN, NST>::SMEM);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static DeviceOnce once;
+  if (cudaError_t e = device_once(once, [](int) {
+        return cudaFuncSetAttribute(gemm_tf32x3_kernel<BN, NST>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, Tf32Cfg<BN, NST>::SMEM);
+      });
+      e != cudaSuccess)
+    return e;
   CUtensorMap ta, tb;
   if (!make_tmap_2d(&ta, 0, x, M, K, ldx, kBK, kBM) || !make_tmap_2d(&tb, 0, W, N, K, K, kBK, BN))
     return cudaErrorInvalidValue;
@@ -706,8 +696,6 @@ cudaError_t launch_cfg(GemmCfg c, int M, int N, int K, const float* x, int ldx, 
   if (c.bn == 64 && c.stages == 2) return launch_bn<64, 2>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return cudaErrorInvalidValue;
 }
-
-int g_sms = 0;
 
 }  // namespace
 
@@ -746,17 +734,13 @@ cudaError_t launch_linear_f32_tc(int M, int N, int K, const float* x, int ldx, c
   if (K <= 0 || (K % 4) || (N % 64) || (ldx % 4) || (ldy % 4) || (reinterpret_cast<uintptr_t>(x) & 15) ||
       (reinterpret_cast<uintptr_t>(W) & 15) || (reinterpret_cast<uintptr_t>(y) & 15))
     return cudaErrorInvalidValue;
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  const int sms_n = device_sms();
   if (cfg.bn) {
     if (N % cfg.bn) return cudaErrorInvalidValue;
     return launch_cfg(cfg, M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   }
   const int mt = (M + kBM - 1) / kBM;
-  if (N % 128 == 0 && mt * (N / 128) >= g_sms) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
+  if (N % 128 == 0 && mt * (N / 128) >= sms_n) return launch_bn<128, 3>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
   return launch_bn<64, 4>(M, N, K, x, ldx, W, bias, relu, y, ldy, err, s);
 }
 
@@ -768,17 +752,13 @@ cudaError_t launch_linear_f32_tc_presplit(int M, int N, int K, const float* xh, 
   for (const void* p : {static_cast<const void*>(xh), static_cast<const void*>(xl), static_cast<const void*>(wh),
                         static_cast<const void*>(wl), static_cast<const void*>(yh), static_cast<const void*>(yl)})
     if (reinterpret_cast<uintptr_t>(p) & 15) return cudaErrorInvalidValue;
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  const int sms_n = device_sms();
   if (cfg.bn) {
     if (N % cfg.bn) return cudaErrorInvalidValue;
     return launch_presplit_cfg(cfg, M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
   }
   const int mt = (M + kBM - 1) / kBM;
-  if (N % 128 == 0 && mt * (N / 128) >= g_sms)
+  if (N % 128 == 0 && mt * (N / 128) >= sms_n)
     return launch_presplit_bn<128, 3>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
   return launch_presplit_bn<64, 4>(M, N, K, xh, xl, ldx, wh, wl, bias, relu, yh, yl, ldy, err, s);
 }

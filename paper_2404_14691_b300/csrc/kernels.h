@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,6 +30,32 @@ bool host_csr_valid(const sage_host_invocation& v, int T);
 // Kernels launched by this library so far (all pools, all threads).
 void count_launch(int n = 1);
 int64_t launches();
+
+// Kernel function attributes (shared-memory size, carve-out) are set per device:
+// a launcher runs its set-up once on every device that uses it, from any thread.
+constexpr int kMaxDevices = 64;
+struct DeviceOnce {
+  std::atomic<uint64_t> done{0};
+  std::mutex mu;
+};
+// Runs init(dev) the first time the current device reaches this DeviceOnce; *dev
+// (optional) receives the current device.  init's error is returned and the set-up
+// is retried on the next call.
+template <class F>
+cudaError_t device_once(DeviceOnce& o, F&& init, int* dev_out = nullptr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (dev_out) *dev_out = dev;
+  const uint64_t bit = uint64_t(1) << dev;
+  if (o.done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  std::lock_guard<std::mutex> g(o.mu);
+  if (o.done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  const cudaError_t e = init(dev);
+  if (e == cudaSuccess) o.done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
+// SMs of the current device (looked up once per device).
+int device_sms();
 
 // Embedding-bag sum over a fused batch (the gather of the function).
 struct GatherArgs {

@@ -386,15 +386,7 @@ __global__ void __launch_bounds__(256) head_kernel(const __grid_constant__ InvTa
   }
 }
 
-int g_sms = 0;
-int sms() {
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  return g_sms;
-}
+int sms() { return device_sms(); }
 
 }  // namespace
 

@@ -36,12 +36,11 @@ namespace {
 
 constexpr size_t kScratchBytes = size_t(64) << 20;  // 64 MiB
 constexpr size_t kErrBytes = 256;                    // error word, cleared by every call
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 std::mutex g_scratch_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
+void* g_scratch_ptr[sage::kMaxDevices] = {};
 
 sage_status noalloc_fail(sage_status st, const char* msg) {
   sage::set_last_error(msg);
@@ -57,7 +56,7 @@ bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 sage_status scratch_base(char** out, int* dev_out) {
   char msg[160];
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= sage::kMaxDevices)
     return noalloc_fail(SAGE_ERR_CUDA, "cudaGetDevice failed");
   std::lock_guard<std::mutex> g(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
