@@ -85,7 +85,7 @@ typedef void* (*sage_dev_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*sage_dev_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 
 typedef struct {
-    int device;                    /* CUDA ordinal */
+    int device;                    /* CUDA ordinal; pools on several devices may share a process */
     size_t budget_bytes;           /* device bytes the pool may hold for read-only data and
                                       workspaces; 0 = free memory at creation minus 2 GiB */
     size_t staging_chunk_bytes;    /* pinned staging chunk size; 0 = 64 MiB (rounded to 4 KiB) */
