@@ -302,12 +302,15 @@ sage_status sage_fn_debug_copy(sage_fn fn, int which, int plane, void* dst, size
  * device copy and workspace and returns the budget -- or, with host_cache_bytes,
  * first keeps the read-only data in host memory: the first two stages of the
  * paper's multi-stage resource exit (Sec. 6.3).  SAGE_ERR_INVALID for a bad
- * handle. */
+ * handle; SAGE_ERR_CUDA when waiting for that work reported a device failure that
+ * no earlier call had surfaced (the memory and the handle are released anyway). */
 sage_status sage_release(sage_fn fn);
 
 /* Destroy an empty pool: the daemon's end, after every function it served has
  * exited (the last stage of Sec. 6.3).  SAGE_ERR_BUSY while any reference is
- * live (nothing is freed then); the host cache is freed. */
+ * live (nothing is freed then); the host cache is freed.  SAGE_ERR_CUDA when the
+ * pool's last staging or allocation work reported a device failure (the pool is
+ * destroyed anyway). */
 sage_status sage_pool_destroy(sage_pool pool);
 
 /* Copy the pool's counters into *out.  Read-only bytes and workspace bytes are
@@ -578,7 +581,8 @@ sage_status sage_partition_create(int device, int groups, int min_sms, sage_part
 int sage_partition_groups(sage_partition p);
 /* Group g's stream (a cudaStream_t owned by the partition) and its SM count. */
 sage_status sage_partition_stream(sage_partition p, int group, void** stream, int* sms);
-/* Waits for the groups' streams, then destroys them and the green contexts. */
+/* Waits for the groups' streams, then destroys them and the green contexts;
+ * SAGE_ERR_CUDA when that wait reported a device failure (destroyed anyway). */
 sage_status sage_partition_destroy(sage_partition p);
 
 #ifdef __cplusplus

@@ -13,9 +13,10 @@ from __future__ import annotations
 import ctypes
 from typing import Optional, Sequence
 
-from ._native import (DEV_ALLOC_FN, DEV_FREE_FN, SAGE_BF16, SAGE_F32, SAGE_OK, SAGE_PENDING, SAGE_READONLY,
-                      STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, KernelTime, PoolConfig, PoolStats,
-                      Request, RequestResult, SageError, ServeConfig, ServeStats, ShareStats, check, lib)
+from ._native import (DEV_ALLOC_FN, DEV_FREE_FN, SAGE_BF16, SAGE_ERR_BUSY, SAGE_F32, SAGE_OK, SAGE_PENDING,
+                      SAGE_READONLY, STATUS_NAMES, DataDesc, FnDesc, HostInvocation, Invocation, KernelTime,
+                      PoolConfig, PoolStats, Request, RequestResult, SageError, ServeConfig, ServeStats, ShareStats,
+                      check, lib)
 
 __all__ = ["Pool", "Function", "SageError", "SAGE_F32", "SAGE_BF16", "embedding_bag_sum", "linear",
            "kernel_launches", "profile_enable", "profile_read", "torch_allocator_hooks", "serve", "Share",
@@ -212,9 +213,11 @@ class Function:
 
     def release(self) -> None:
         if self.handle is not None:
-            check(lib().sage_release(self.handle), "sage_release")
-            self.handle = None
+            # the library releases the handle even when it reports a device failure
+            h, self.handle = self.handle, None
+            st = lib().sage_release(h)
             self._keep = None
+            check(st, "sage_release")
 
 
 class Pool:
@@ -258,8 +261,10 @@ class Pool:
 
     def destroy(self) -> None:
         if self.handle is not None:
-            check(lib().sage_pool_destroy(self.handle), "sage_pool_destroy")
-            self.handle = None
+            st = lib().sage_pool_destroy(self.handle)
+            if st != SAGE_ERR_BUSY:      # destroyed, also when it reports a device failure
+                self.handle = None
+            check(st, "sage_pool_destroy")
 
 
 def tuning_set(kind: int, rows: int, N: int, K: int, bn: int, stages: int) -> None:
@@ -370,5 +375,5 @@ class Partition:
 
     def destroy(self) -> None:
         if self.handle is not None:
-            check(lib().sage_partition_destroy(self.handle), "sage_partition_destroy")
-            self.handle = None
+            h, self.handle = self.handle, None
+            check(lib().sage_partition_destroy(h), "sage_partition_destroy")

@@ -181,9 +181,16 @@ sage_status sage_partition_stream(sage_partition p, int group, void** stream, in
 
 sage_status sage_partition_destroy(sage_partition p) {
   if (!p) return sage::set_last_error("null partition"), SAGE_ERR_INVALID;
-  for (cudaStream_t s : p->first) cudaStreamSynchronize(s);
+  cudaError_t ce = cudaSuccess;
+  for (cudaStream_t s : p->first) {
+    const cudaError_t c = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = c;
+  }
   delete p->p;
   delete p;
+  if (ce != cudaSuccess)
+    return sage::set_last_error("partition destroyed, but work on its streams had failed on the device"),
+           SAGE_ERR_CUDA;
   return SAGE_OK;
 }
 

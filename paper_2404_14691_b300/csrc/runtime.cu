@@ -722,8 +722,14 @@ bool same_shape(const Entry* e, const sage_fn_desc* d) {
   return e->tables_bytes == d->tables.bytes && e->weights_bytes == d->weights.bytes;
 }
 
-// Free an entry's device memory after all of its work finished.
-void destroy_entry(sage_pool_s* P, Entry* e) {
+// Free an entry's device memory after all of its work finished.  Returns the first
+// error the waits for that work reported (a kernel or copy of the function that
+// failed after its caller last checked); the memory is freed either way.
+cudaError_t destroy_entry(sage_pool_s* P, Entry* e) {
+  cudaError_t first = cudaSuccess;
+  auto note = [&](cudaError_t c) {
+    if (c != cudaSuccess && first == cudaSuccess) first = c;
+  };
   if (e->imp) e->imp->interrupt();  // a waiter still blocked on the owner returns (failed)
   {
     std::unique_lock<std::mutex> l(e->smu);
@@ -731,20 +737,20 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
     e->scv.wait(l, [&] { return e->sstate != 0; });
   }
   if (e->imp_waiter.joinable()) e->imp_waiter.join();
-  if (e->ready) cudaEventSynchronize(e->ready);
+  if (e->ready) note(cudaEventSynchronize(e->ready));
   for (auto& s : e->slots) {
     if (s.done) {
-      cudaEventSynchronize(s.done);
+      note(cudaEventSynchronize(s.done));
       cudaEventDestroy(s.done);
     }
     if (s.branch) {
-      cudaStreamSynchronize(s.branch);
+      note(cudaStreamSynchronize(s.branch));
       cudaStreamDestroy(s.branch);
     }
     if (s.fork) cudaEventDestroy(s.fork);
     if (s.join) cudaEventDestroy(s.join);
     if (s.h2d) {
-      cudaStreamSynchronize(s.h2d);
+      note(cudaStreamSynchronize(s.h2d));
       cudaStreamDestroy(s.h2d);
     }
     if (s.copied) cudaEventDestroy(s.copied);
@@ -811,7 +817,7 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
   }
   P->dev_free(e->d_wsplit, e->wsplit_bytes, P->alloc);
   P->dev_free(e->d_err, 256, P->alloc);
-  cudaStreamSynchronize(P->alloc);
+  note(cudaStreamSynchronize(P->alloc));
   e->imp.reset();  // unmap the owner's copy after the last use above
   if (e->ready) cudaEventDestroy(e->ready);
   {
@@ -819,6 +825,7 @@ void destroy_entry(sage_pool_s* P, Entry* e) {
     P->used -= e->reserved;
   }
   delete e;
+  return first;
 }
 
 // Wait (host) until the entry's setup finished and all staging copies are queued.
@@ -1885,7 +1892,10 @@ sage_status sage_release(sage_fn f) {
   delete f;
   if (e) {
     SAGE_CK(cudaSetDevice(P->device));
-    destroy_entry(P, e);
+    const cudaError_t ce = destroy_entry(P, e);
+    if (ce != cudaSuccess)
+      return fail(SAGE_ERR_CUDA, "released, but work of the function had failed on the device: %s",
+                  cudaGetErrorString(ce));
   }
   return SAGE_OK;
 }
@@ -1903,8 +1913,9 @@ sage_status sage_pool_destroy(sage_pool P) {
   P->qcv.notify_all();
   if (P->stager.joinable()) P->stager.join();
   cudaSetDevice(P->device);
-  cudaStreamSynchronize(P->side);
-  cudaStreamSynchronize(P->alloc);
+  cudaError_t ce = cudaStreamSynchronize(P->side);
+  const cudaError_t ce2 = cudaStreamSynchronize(P->alloc);
+  if (ce == cudaSuccess) ce = ce2;
   for (auto& kv : P->hcache) free_image(P, kv.second);
   P->hcache.clear();
   for (size_t i = 0; i < P->ring.size(); ++i) {
@@ -1915,6 +1926,9 @@ sage_status sage_pool_destroy(sage_pool P) {
   cudaStreamDestroy(P->alloc);
   P->workers.reset();
   delete P;
+  if (ce != cudaSuccess)
+    return fail(SAGE_ERR_CUDA, "pool destroyed, but its staging work had failed on the device: %s",
+                cudaGetErrorString(ce));
   return SAGE_OK;
 }
 

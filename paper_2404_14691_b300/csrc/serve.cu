@@ -161,7 +161,7 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
           if (victim < 0 || F[g].last_active < F[victim].last_active) victim = g;
         }
         if (victim < 0) break;
-        sage_release(F[victim].h);
+        if (sage_release(F[victim].h) != SAGE_OK) result = SAGE_ERR_CUDA;
         F[victim].h = nullptr;
         F[victim].ready = false;
         st.evictions++;
@@ -274,7 +274,7 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
     if (cfg.linger_s >= 0) {
       for (auto& S : F) {
         if (S.h && S.ready && !S.inflight && S.queue.empty() && t - S.last_active > cfg.linger_s) {
-          sage_release(S.h);
+          if (sage_release(S.h) != SAGE_OK) result = SAGE_ERR_CUDA;
           S.h = nullptr;
           S.ready = false;
           st.evictions++;
@@ -300,7 +300,7 @@ extern "C" sage_status sage_serve(sage_pool pool, const sage_fn_desc* fns, int n
     for (auto& L : S.lanes) {
       if (L.busy) cudaEventSynchronize(L.ev);
     }
-    if (S.h) sage_release(S.h);
+    if (S.h && sage_release(S.h) != SAGE_OK && result == SAGE_OK) result = SAGE_ERR_CUDA;
   }
   st.wall_s = now_s();
   std::vector<double> all, cold, warm;
