@@ -821,13 +821,6 @@ def cold_run_summary(reqs, results, n_fns):
     return out
 
 
-# serving pools launch each batch's chain directly (False) or as a CUDA-graph replay;
-# set from --serve-graphs.  Direct is the default: capturing and updating a graph per
-# small batch costs the host more than the launches it replaces (warm p50 0.23-0.24 ms
-# direct against 0.36-0.37 ms replayed, 200 requests/s, both forms).
-SERVE_GRAPHS = [False]
-
-
 def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), repeats=1, **kw):
     """Replay one trace per mode on a fresh pool: cold (every function prepared at its
     first request: setup inside the latencies) or warm (every function resident and
@@ -845,13 +838,12 @@ def serve_modes(specs, reqs, out, warm, modes=(("served", 0), ("plain", 1)), rep
     res, outs = {}, {}
     order = list(modes) if repeats == 1 else [("discard", modes[0][1])] + list(modes) + list(reversed(modes))
     lanes = kw.pop("lanes_per_fn", 2)
-    graphs = kw.pop("graphs", SERVE_GRAPHS[0])
     for mode, mbi in order:
         if not warm:
             # every cold run starts from host cores at speed, so that the modes compare
             # their setups rather than the host's warm-up
             warm_host_cores(1.5)
-        pool = sage.Pool(device=0, graphs=graphs)
+        pool = sage.Pool(device=0)
         held = []
         if warm:
             held = [pool.prepare(**workload.prepare_kwargs(s)) for s in specs]
@@ -909,7 +901,6 @@ def serving_summary(args):
     return {"workload": "serving: %d requests, Poisson 200/s over 4 bf16 functions (8x1Mx64, 26x1Mx128, "
                         "26x4Mx128, 52x2Mx64; %.1f GB read-only), B~round(LogNormal(ln256,1)), L~U[1,100]; "
                         "requests from pinned host buffers" % (args.requests, total_ro / 1e9),
-            "launch": "one CUDA-graph replay per batch" if SERVE_GRAPHS[0] else "direct kernel launches",
             "cold_start": cold, "warm": warm, "warm_10000_per_s": high, "warm_saturation": sat,
             "outputs_identical": same,
             "served_beats_plain": {"cold_start": dict(beats(cold), after_setup_p99=cold["served"].get(
@@ -1332,8 +1323,6 @@ def main():
     ap.add_argument("--stress-functions", type=int, default=16)
     ap.add_argument("--stress-invocations", type=int, default=256)
     ap.add_argument("--share-reps", type=int, default=2)
-    ap.add_argument("--serve-graphs", choices=["on", "off"], default="off",
-                    help="serving pools: each batch's launch chain as one CUDA-graph replay, or direct launches")
     ap.add_argument("--gather-top0", choices=["default", "on", "off"], default="default",
                     help="fp32 functions: pin the gather + first-top-layer fusion on or off")
     ap.add_argument("--no-extras", action="store_true",
@@ -1343,7 +1332,6 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    SERVE_GRAPHS[0] = args.serve_graphs == "on"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

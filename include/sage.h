@@ -102,11 +102,11 @@ typedef struct {
                                       used images evicted) and a later prepare of the key re-stages
                                       from there at link speed instead of calling its producer.
                                       0 = off (release frees everything). */
-    int graphs;                    /* 1 = sage_invoke / sage_invoke_batch / the host-buffer batches (and
-                                      so sage_serve) capture each batch's launch chain into a CUDA graph
-                                      (updated in place while the kernels stay the same) and launch it in
-                                      one call; 0 = direct launches.  Streams of an SM partition always
-                                      launch directly */
+    int graphs;                    /* 1 = sage_invoke / sage_invoke_batch capture each batch's launch
+                                      chain into a CUDA graph (updated in place while the kernels stay
+                                      the same) and launch it in one call; 0 = direct launches.  Host-buffer
+                                      batches (and sage_serve) and streams of an SM partition always launch
+                                      directly */
     int exportable;                /* 1 = read-only items are allocated as exportable physical memory
                                       (CUDA virtual memory management, POSIX file-descriptor handles)
                                       so that sage_share_start can map them into other processes;

@@ -1733,16 +1733,10 @@ sage_status sage::host_batch_async(sage_fn f, const sage_host_invocation* invs, 
     SAGE_CK(cudaEventRecord(sl->copied, sl->h2d));
     SAGE_CK(cudaStreamWaitEvent(s, sl->copied, 0));
     SAGE_CK(cudaStreamWaitEvent(s, e->ready, 0));
-    // the chain as one CUDA-graph launch when the pool replays graphs (as run_batch)
-    const bool confined = sage::stream_is_confined(s);
-    if (e->pool->graphs && !confined && !g_prof_on.load(std::memory_order_relaxed)) {
-      st = capture_chain(e, *sl, *tab);
-      if (st != SAGE_OK) return st;
-      SAGE_CK(cudaGraphLaunch(sl->exec, s));
-    } else {
-      st = launch_chain(e, *sl, *tab, s, confined);
-      if (st != SAGE_OK) return st;
-    }
+    // direct launches: replaying the chain as a CUDA graph (capture + update per batch)
+    // measured slower here, where the host's time per batch is on the critical path
+    st = launch_chain(e, *sl, *tab, s, sage::stream_is_confined(s));
+    if (st != SAGE_OK) return st;
     // D2H of the outputs, merged where the host outputs are adjacent
     runs.clear();
     size_t ou2 = 0;
