@@ -12,7 +12,9 @@ the whole path (bottom MLP, gather, top MLP, head).  The same line carries the
 uniform-index gather control (26 x 4M x 128, no Zipf reuse), the fp32 batching
 workload (64 invocations of 8 x 100,000 x 64 fp32) and the serving workload's
 latencies including setup (2,000 Poisson requests over 4 functions, served vs one
-invocation per launch).  Prints one JSON line (rank 0).
+invocation per launch), and the CPU oracle's rate as cpu_baseline -- the reference
+arm (`--impl reference`, the fp64 oracle on the host cores) run in a fresh process.
+Prints one JSON line (rank 0).
 """
 import argparse
 import json
