@@ -132,3 +132,32 @@ def test_cold_run_summary():
     # after setup: 10, 20 and 5 ms (the warm request is not counted): median 10, p99 20
     assert abs(s["cold_after_setup_p50_ms"] - 10.0) < 1e-6
     assert abs(s["cold_after_setup_p99_ms"] - 20.0) < 1e-6
+
+
+def test_cpu_baseline_is_the_reference_arm_in_a_child_process(monkeypatch):
+    """cpu_baseline runs `bench.py --impl reference` for the same workload in a fresh
+    process (two steps of half the budget each) and reports that line's cpu_baseline."""
+    import argparse
+    import json
+    import subprocess
+    seen = {}
+
+    class Done:
+        returncode = 0
+        stderr = ""
+        stdout = "noise\n" + json.dumps({"impl": "reference", "cpu_baseline": {
+            "value": 2.5, "unit": "invocations/s", "cores": 16, "kind": "oracle", "sample": "fitted"}}) + "\n"
+
+    def fake_run(cmd, **kw):
+        seen["cmd"], seen["env"] = cmd, kw.get("env", {})
+        return Done()
+
+    monkeypatch.setattr(subprocess, "run", fake_run)
+    monkeypatch.setenv("RANK", "3")
+    cb = bench.cpu_baseline(argparse.Namespace(workload="c3", cpu_budget_s=12.0))
+    cmd = seen["cmd"]
+    assert cmd[cmd.index("--impl") + 1] == "reference" and cmd[cmd.index("--workload") + 1] == "c3"
+    assert float(cmd[cmd.index("--ref-step-s") + 1]) == 6.0 and cmd[cmd.index("--steps") + 1] == "2"
+    assert "RANK" not in seen["env"]                      # the child is a single process
+    assert cb["value"] == 2.5 and cb["kind"] == "oracle" and cb["sample"].endswith("fitted")
+    assert "fresh process" in cb["sample"]
